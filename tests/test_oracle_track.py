@@ -1,0 +1,95 @@
+"""Pins for the oracle tracker (Section 2) on systems whose solutions are known
+in closed form or from a textbook routine."""
+import numpy as np
+import pytest
+
+import synth
+from exact import Cx, cx_from, poly_value
+from fractions import Fraction as Fr
+from match import match_sets, to_complex
+
+
+def _diag_system(cvals):
+    n = len(cvals)
+    exps = []
+    coef = []
+    for i, c in enumerate(cvals):
+        a = [0] * n
+        a[i] = 2
+        exps += [a, [0] * n]
+        coef += [[1.0, 0.0], [-c.real, -c.imag]]
+    return synth.System(n, n, np.full(n, 2, np.int32), np.array(exps, np.int8), np.array(coef))
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_diagonal_system_closed_form(oracle_lib, L):
+    """f_i = x_i^2 - c_i: the 2^n endpoints are all sign choices of sqrt(c_i)."""
+    c = np.array([0.3 + 0.8j, -1.1 + 0.2j, 0.5 - 0.9j])
+    s = _diag_system(c)
+    out = oracle_lib.track(s, [2, 2, 2], synth.random_gamma(1), np.arange(8), L)
+    assert np.all(out["status"] == 1)
+    r = np.sqrt(c)
+    expect = np.array([[r[0] * (1 - 2 * ((p >> 0) & 1)), r[1] * (1 - 2 * ((p >> 1) & 1)),
+                        r[2] * (1 - 2 * ((p >> 2) & 1))] for p in range(8)])
+    ok, worst = match_sets(to_complex(out["x_end"]), expect, 1e-13)
+    assert ok, worst
+    # residual of every endpoint, exactly
+    for p in range(8):
+        for i in range(3):
+            z = cx_from(out["x_end"][i, :, :, p])
+            res = z * z - Cx(Fr(c[i].real), Fr(c[i].imag))
+            assert res.absf() <= {1: 1e-14, 2: 1e-28, 4: 1e-55}[L]
+
+
+def test_univariate_roots_match_companion_matrix(oracle_lib):
+    s = synth.total_degree_system(77, 1, 6, 7)  # dense univariate of degree 6
+    out = oracle_lib.track(s, [6], synth.random_gamma(2), np.arange(6), 1)
+    assert np.all(out["status"] == 1)
+    coeffs = np.zeros(7, complex)
+    for a, cf in zip(s.exps[:, 0], s.coef):
+        coeffs[6 - a] += cf[0] + 1j * cf[1]
+    roots = np.roots(coeffs)
+    ok, worst = match_sets(to_complex(out["x_end"]), roots[:, None], 1e-10)
+    assert ok, worst
+
+
+def _dense(seed, n, d):
+    from math import comb
+    return synth.total_degree_system(seed, n, d, comb(n + d, d))
+
+
+@pytest.mark.slow
+def test_dense_generic_system_reaches_bezout_and_precisions_agree(oracle_lib):
+    """All monomials of degree <= 2 present with random coefficients: all 2^n
+    paths converge (the Bezout number is attained); D, DD and QD endpoint sets
+    agree to 1e-10; every QD endpoint has an exact residual below 1e-40."""
+    s = _dense(5, 3, 2)
+    ends = {}
+    for L in (1, 2, 4):
+        out = oracle_lib.track(s, [2, 2, 2], synth.random_gamma(3), np.arange(8), L)
+        assert np.all(out["status"] == 1), (L, out["status"])
+        ends[L] = out
+    for L in (2, 4):
+        ok, worst = match_sets(to_complex(ends[1]["x_end"]), to_complex(ends[L]["x_end"]), 1e-10)
+        assert ok, (L, worst)
+    coefs = [Cx(Fr(c[0]), Fr(c[1])) for c in s.coef]
+    m = s.n_terms[0]
+    for p in range(8):
+        xp = [cx_from(ends[4]["x_end"][i, :, :, p]) for i in range(3)]
+        for j in range(3):
+            r = poly_value(coefs[j * m:(j + 1) * m], s.exps[j * m:(j + 1) * m], xp)
+            assert r.absf() <= 1e-40
+
+
+def test_plain_c0_shape_runs_and_converged_endpoints_are_solutions(oracle_lib):
+    s = synth.config_system("c0_plain_d")
+    out = oracle_lib.track(s, [2] * 6, synth.random_gamma(0), np.arange(64), 1,
+                           oracle_lib.default_params(1, h_min=1e-6))
+    assert np.all(out["status"] == 1)  # with a small step floor every path converges
+    X = to_complex(out["x_end"])
+    # distinct endpoints: no two paths ended at the same solution
+    ok, _ = match_sets(X, X, 0)
+    D = np.max(np.abs(X[:, None] - X[None]), axis=2) + np.eye(64) * 1e9
+    assert D.min() > 1e-6
+    val, _ = oracle_lib.eval_(s, out["x_end"])
+    assert np.max(np.abs(val[:, 0, 0] + 1j * val[:, 1, 0])) < 1e-10
