@@ -1,0 +1,315 @@
+"""Benchmark of the hot path: evaluation and differentiation of a polynomial
+system at many points (the 65,536-point sweep of a 32-variable system with
+2,048 monomials of 2-8 variables), in complex double, double double and quad
+double -- one step is one pass over the batch in all three precisions.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  ``value`` is whole-job eval-diff points per second, a
+point counting once when it has been evaluated (values and full Jacobian) in
+all three precisions.  For N > 1 (torchrun) every rank evaluates its own batch
+(weak scaling, no collective on the data path).  ``--impl reference`` times
+the CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "eval-diff pts/s (values + 32x32 Jacobian per point, complex D+DD+QD)"
+UNIT = "pts/s"
+WORKLOAD = "c1_evaldiff"
+PRECISIONS = (1, 2, 4)
+NAMES = {1: "D", 2: "DD", 4: "QD"}
+
+# FP64 instructions per complex operation of the device arithmetic
+# (paper_1505_00383_gb300/csrc/ht_mp.cuh): multiply, add, and accumulate of a
+# product scaled by a small integer exponent.
+OPS = {1: dict(cmul=4, cadd=2, caxpy=2),
+       2: dict(cmul=38, cadd=22, caxpy=34),
+       4: dict(cmul=448, cadd=140, caxpy=270)}
+
+
+def eval_ops_per_point(system, L):
+    """FP64 instructions the reverse-mode evaluation of one point needs:
+    per monomial with k variables of exponents a_r: sum(a_r - 1) multiplications
+    for the common factor, 3k - 3 (k >= 2; 1 for k = 1) for value and
+    derivatives, one add for the value and one (scaled) add per derivative."""
+    o = OPS[L]
+    tot = 0
+    for a in system.exps.astype(int):
+        a = a[a > 0]
+        k = a.size
+        if k == 0:
+            tot += o["cadd"]
+            continue
+        ncm = int((a - 1).sum()) + (1 if k == 1 else 3 * k - 3)
+        tot += ncm * o["cmul"] + o["cadd"] + sum(o["cadd"] if e == 1 else o["caxpy"] for e in a)
+    return tot
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--n-pts", type=int, default=65536)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons while running."""
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in rows if len(r) > 2 and r[1].strip().replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 2 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if len(r) > 5 + k and "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def _traffic(L):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    sources are unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "evaldiff_c1_65536pts.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"sources_sha256:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != _kernel_sha():
+        return None
+    m = re.search(r"traffic_bytes_per_launch_%s:\s*([0-9.eE+]+)" % NAMES[L], txt)
+    return float(m.group(1)) if m else None
+
+
+def _kernel_sha():
+    h = hashlib.sha256()
+    for f in ("ht_evaldiff.cu", "ht_mp.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1505_00383_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def cpu_oracle_rate(system, budget_pts, threads=0, seed=77):
+    """Oracle throughput in the metric's unit on a bounded sample: for each
+    precision, budget_pts[L] points evaluated by the oracle's reverse mode."""
+    import oracle
+    oracle.build()
+    per_pt = 0.0
+    for L in PRECISIONS:
+        n = budget_pts[L]
+        x = synth.unit_points(seed + L, system.n_vars, n, L)
+        t0 = time.perf_counter()
+        oracle.eval_(system, x, n_threads=threads)
+        per_pt += (time.perf_counter() - t0) / n
+    return 1.0 / per_pt
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    system = synth.config_system(WORKLOAD)
+    cores = os.cpu_count() or 1
+    budget = {1: 512, 2: 48, 4: 8}
+    for _ in range(a.warmup):
+        cpu_oracle_rate(system, {1: 16, 2: 4, 4: 1}, threads=cores)
+    rates = [cpu_oracle_rate(system, budget, threads=cores, seed=100 + s) for s in range(a.steps)]
+    v = float(statistics.median(rates))
+    sample = "per step: %d D + %d DD + %d QD points of the %d-point sweep" % (budget[1], budget[2], budget[4],
+                                                                               a.n_pts)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": a.n_pts / v * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64 (D, DD, QD limbs)", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_vars": 32, "n_polys": 32, "monomials": 2048, "n_pts": a.n_pts},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1505_00383_gb300 import _build
+    _build.build()
+    from paper_1505_00383_gb300 import ht
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+
+    system = synth.config_system(WORKLOAD)
+    n = a.n_pts
+    sys_h, xs, vals, jacs = {}, {}, {}, {}
+    for L in PRECISIONS:
+        sys_h[L] = ht.system_from(system, L)
+        xs[L] = torch.from_numpy(synth.unit_points(1000 + 7 * rank + L, system.n_vars, n, L)).to(dev)
+        vals[L] = torch.empty((system.n_polys, 2, L, n), dtype=torch.float64, device=dev)
+        jacs[L] = torch.empty((system.n_polys, system.n_vars, 2, L, n), dtype=torch.float64, device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
+
+    fp64_peak = ht.ht_bench_fp64_rate(100)
+
+    def step(events=None):
+        for L in PRECISIONS:
+            if events is not None:
+                events[L][0].record(stream)
+            ht.ht_eval_diff(sys_h[L], n, xs[L], vals[L], jacs[L], stream)
+            if events is not None:
+                events[L][1].record(stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ev = [{L: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for L in PRECISIONS}
+          for _ in range(a.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        t_wall = time.perf_counter()
+        for s in range(a.steps):
+            flush.zero_()
+            step(ev[s])
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    launch_ms = {L: [ev[s][L][0].elapsed_time(ev[s][L][1]) for s in range(a.steps)] for L in PRECISIONS}
+    ms_step = sum(statistics.mean(launch_ms[L]) for L in PRECISIONS)
+    if world > 1:
+        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step = float(t.item())
+    value = world * n / (ms_step * 1e-3)
+
+    # end to end through the host-buffer entry point (pinned host memory)
+    e2e = None
+    if not a.no_e2e:
+        hx = {L: xs[L].cpu().pin_memory() for L in PRECISIONS}
+        hv = {L: torch.empty(vals[L].shape, dtype=torch.float64).pin_memory() for L in PRECISIONS}
+        hj = {L: torch.empty(jacs[L].shape, dtype=torch.float64).pin_memory() for L in PRECISIONS}
+        for L in PRECISIONS:  # warm-up (workspace allocation)
+            ht.ht_eval_diff_host(sys_h[L], n, hx[L], hv[L], hj[L], stream)
+        del vals, jacs
+        ts = []
+        for s in range(max(1, min(a.steps, 3))):
+            t0 = time.perf_counter()
+            for L in PRECISIONS:
+                ht.ht_eval_diff_host(sys_h[L], n, hx[L], hv[L], hj[L], stream)
+            ts.append(time.perf_counter() - t0)
+        e2e_s = statistics.mean(ts)
+        if world > 1:
+            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": world * n / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(hx[L].numel() * 8 for L in PRECISIONS)),
+               "d2h_bytes_per_step": int(sum((hv[L].numel() + hj[L].numel()) * 8 for L in PRECISIONS))}
+
+    # roofline of the dominant kernel (the one with the largest share of the step)
+    dom = max(PRECISIONS, key=lambda L: statistics.mean(launch_ms[L]))
+    ops_launch = eval_ops_per_point(system, dom) * n
+    achieved = ops_launch / (statistics.mean(launch_ms[dom]) * 1e-3)
+    tr = _traffic(dom)
+    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12,
+                "unit": "T FP64-instr/s", "frac": achieved / fp64_peak,
+                "traffic": tr, "kernel": "evaldiff_kernel<%d> (%s)" % (dom, NAMES[dom]),
+                "peak_source": "measured live: ht_bench_fp64_rate (DFMA chains on all SMs)"}
+    per_prec = {}
+    for L in PRECISIONS:
+        m = statistics.mean(launch_ms[L])
+        ops = eval_ops_per_point(system, L) * n
+        per_prec[NAMES[L]] = {"ms": m, "pts_per_s": n / (m * 1e-3), "fp64_frac": ops / (m * 1e-3) / fp64_peak,
+                              "out_GB_per_s": (system.n_polys * (system.n_vars + 1) * 16 * L * n) / (m * 1e-3) / 1e9}
+
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cores = os.cpu_count() or 1
+        budget = {1: 1024, 2: 64, 4: 16}
+        v = cpu_oracle_rate(system, budget, threads=cores)
+        cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": "%d D + %d DD + %d QD points of the sweep, all host cores" % (budget[1], budget[2],
+                                                                                         budget[4])}
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64 (D, DD, QD limbs)", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_vars": 32, "n_polys": 32, "monomials": 2048,
+                       "monomial_vars": "2-8", "exponents": "1-3", "n_pts_per_gpu": n,
+                       "l2": "flushed (512 MB write) before every timed step; outputs 1.1-4.5 GB per launch",
+                       "parallelism": "independent batch per GPU"},
+            "per_precision": per_prec, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": a.steps * len(PRECISIONS), "clocks": clk.summary(),
+            "wall_s_timed_region": t_wall,
+        }))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)

@@ -1,0 +1,228 @@
+// C ABI entry points: argument checks, system upload, dispatch.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "ht_internal.h"
+
+namespace ht {
+
+static thread_local std::string g_err;
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return code;
+}
+void clear_error() { g_err.clear(); }
+int cuda_fail(cudaError_t e, const char* what) {
+  return set_error(HT_ECUDA, "%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+}
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  int dev = 0;
+  cudaGetDevice(&dev);
+  return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
+}
+int sm_count() {
+  int dev = 0, n = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  return n > 0 ? n : 1;
+}
+
+}  // namespace ht
+
+using namespace ht;
+
+extern "C" {
+
+const char* ht_last_error(void) { return g_err.c_str(); }
+
+int ht_create_system(int n_vars, int n_polys, const int32_t* n_terms, const int8_t* exps, const double* coef,
+                     int limbs, ht_system** out) {
+  clear_error();
+  if (!out) return set_error(HT_EINVAL, "ht_create_system: out is NULL");
+  *out = nullptr;
+  if (n_vars < 1 || n_vars > 255) return set_error(HT_EINVAL, "ht_create_system: n_vars=%d not in 1..255", n_vars);
+  if (n_polys < 1) return set_error(HT_EINVAL, "ht_create_system: n_polys=%d < 1", n_polys);
+  if (limbs != 1 && limbs != 2 && limbs != 4) return set_error(HT_EINVAL, "ht_create_system: limbs=%d", limbs);
+  if (!n_terms || !exps || !coef) return set_error(HT_EINVAL, "ht_create_system: NULL array");
+  ht_system* s = new (std::nothrow) ht_system();
+  if (!s) return set_error(HT_ENOMEM, "ht_create_system: host allocation");
+  s->nv = n_vars;
+  s->np = n_polys;
+  s->limbs = limbs;
+  cudaGetDevice(&s->device);
+  s->h_poly_off.assign(n_polys + 1, 0);
+  for (int j = 0; j < n_polys; ++j) {
+    if (n_terms[j] < 1) {
+      delete s;
+      return set_error(HT_EINVAL, "ht_create_system: n_terms[%d]=%d < 1", j, n_terms[j]);
+    }
+    s->h_poly_off[j + 1] = s->h_poly_off[j] + n_terms[j];
+  }
+  s->M = s->h_poly_off[n_polys];
+  s->n_terms.assign(n_terms, n_terms + n_polys);
+  s->exps.assign(exps, exps + s->M * n_vars);
+  s->coef.assign(coef, coef + s->M * 2 * limbs);
+  s->h_mon_off.assign(s->M + 1, 0);
+  for (int64_t m = 0; m < s->M; ++m) {
+    int k = 0, deg = 0;
+    for (int i = 0; i < n_vars; ++i) {
+      int a = exps[m * n_vars + i];
+      if (a < 0) {
+        delete s;
+        return set_error(HT_EINVAL, "ht_create_system: negative exponent at monomial %lld", (long long)m);
+      }
+      if (a > 0) {
+        s->h_pairs.push_back((uint16_t)(i | (a << 8)));
+        ++k;
+        deg += a;
+        if (a > s->max_exp) s->max_exp = a;
+      }
+    }
+    for (int c = 0; c < 2 * limbs; ++c) {
+      double v = coef[m * 2 * limbs + c];
+      if (!(v == v) || v - v != 0.0) {
+        delete s;
+        return set_error(HT_EINVAL, "ht_create_system: coefficient of monomial %lld is not finite", (long long)m);
+      }
+    }
+    if (k > 64) {
+      delete s;
+      return set_error(HT_EUNSUPPORTED, "ht_create_system: monomial %lld has %d variables (max 64)", (long long)m, k);
+    }
+    if (k > s->max_k) s->max_k = k;
+    if (deg > s->max_deg) s->max_deg = deg;
+    s->h_mon_off[m + 1] = (int32_t)s->h_pairs.size();
+  }
+  s->n_pairs = (int64_t)s->h_pairs.size();
+  // one allocation: coef | poly_off | mon_off | pairs
+  size_t b_coef = (size_t)s->M * 2 * limbs * sizeof(double);
+  size_t b_poly = (size_t)(n_polys + 1) * sizeof(int32_t);
+  size_t b_mon = (size_t)(s->M + 1) * sizeof(int32_t);
+  size_t b_pairs = (size_t)(s->n_pairs + 1) * sizeof(uint16_t);
+  auto up = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  size_t total = up(b_coef) + up(b_poly) + up(b_mon) + up(b_pairs);
+  cudaError_t e = cudaMalloc(&s->d_block, total);
+  if (e != cudaSuccess) {
+    delete s;
+    cudaGetLastError();
+    return set_error(HT_ENOMEM, "ht_create_system: cudaMalloc(%zu): %s", total, cudaGetErrorString(e));
+  }
+  char* base = (char*)s->d_block;
+  s->d_coef = (double*)base;
+  s->d_poly_off = (int32_t*)(base + up(b_coef));
+  s->d_mon_off = (int32_t*)(base + up(b_coef) + up(b_poly));
+  s->d_pairs = (uint16_t*)(base + up(b_coef) + up(b_poly) + up(b_mon));
+  e = cudaMemcpy(s->d_coef, coef, b_coef, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_poly_off, s->h_poly_off.data(), b_poly, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(s->d_mon_off, s->h_mon_off.data(), b_mon, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && s->n_pairs)
+    e = cudaMemcpy(s->d_pairs, s->h_pairs.data(), s->n_pairs * sizeof(uint16_t), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    cudaFree(s->d_block);
+    delete s;
+    return cuda_fail(e, "ht_create_system: upload");
+  }
+  *out = s;
+  return HT_OK;
+}
+
+int ht_destroy_system(ht_system* s) {
+  clear_error();
+  if (!s) return HT_OK;
+  cudaDeviceSynchronize();
+  if (s->d_block) cudaFree(s->d_block);
+  if (s->d_ws) cudaFree(s->d_ws);
+  delete s;
+  return HT_OK;
+}
+
+int ht_system_info(const ht_system* s, int* n_vars, int* n_polys, int* limbs, int64_t* n_monomials) {
+  clear_error();
+  if (!s) return set_error(HT_EINVAL, "ht_system_info: NULL system");
+  if (n_vars) *n_vars = s->nv;
+  if (n_polys) *n_polys = s->np;
+  if (limbs) *limbs = s->limbs;
+  if (n_monomials) *n_monomials = s->M;
+  return HT_OK;
+}
+
+static int check_eval_args(const ht_system* s, int64_t n_pts, const void* x, const void* val, const void* jac,
+                           bool device) {
+  if (!s) return set_error(HT_EINVAL, "eval: NULL system");
+  if (n_pts < 0) return set_error(HT_EINVAL, "eval: n_pts=%lld < 0", (long long)n_pts);
+  if (n_pts == 0) return HT_OK;
+  if (!x || !val || !jac) return set_error(HT_EINVAL, "eval: NULL buffer");
+  if (((uintptr_t)x | (uintptr_t)val | (uintptr_t)jac) & 7)
+    return set_error(HT_EINVAL, "eval: buffers must be 8-byte aligned");
+  if (device && (!is_device_ptr(x) || !is_device_ptr(val) || !is_device_ptr(jac)))
+    return set_error(HT_EINVAL, "eval: x, val and jac must be device memory of the current device");
+  const size_t L = s->limbs;
+  const char* xb = (const char*)x;
+  size_t xbytes = (size_t)s->nv * 2 * L * n_pts * 8;
+  const char* ob[2] = {(const char*)val, (const char*)jac};
+  size_t obytes[2] = {(size_t)s->np * 2 * L * n_pts * 8, (size_t)s->np * s->nv * 2 * L * n_pts * 8};
+  for (int i = 0; i < 2; ++i)
+    if (xb < ob[i] + obytes[i] && ob[i] < xb + xbytes) return set_error(HT_EINVAL, "eval: x overlaps an output");
+  return HT_OK;
+}
+
+int ht_eval_diff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, void* stream) {
+  clear_error();
+  int rc = check_eval_args(s, n_pts, x, val, jac, true);
+  if (rc != HT_OK || n_pts == 0) return rc;
+  return launch_evaldiff(s, n_pts, x, val, jac, (cudaStream_t)stream);
+}
+
+int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double* val_host, double* jac_host,
+                      void* stream) {
+  clear_error();
+  int rc = check_eval_args(s, n_pts, x_host, val_host, jac_host, false);
+  if (rc != HT_OK || n_pts == 0) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t L = s->limbs;
+  size_t bx = (size_t)s->nv * 2 * L * n_pts * 8;
+  size_t bv = (size_t)s->np * 2 * L * n_pts * 8;
+  size_t bj = (size_t)s->np * s->nv * 2 * L * n_pts * 8;
+  size_t need = bx + bv + bj;
+  if (s->ws_bytes < need) {
+    if (s->d_ws) {
+      cudaStreamSynchronize(st);
+      cudaFree(s->d_ws);
+      s->d_ws = nullptr;
+      s->ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&s->d_ws, need);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(HT_ENOMEM, "ht_eval_diff_host: workspace of %zu bytes", need);
+    }
+    s->ws_bytes = need;
+  }
+  double* dx = (double*)s->d_ws;
+  double* dv = (double*)((char*)s->d_ws + bx);
+  double* dj = (double*)((char*)s->d_ws + bx + bv);
+  cudaError_t e = cudaMemcpyAsync(dx, x_host, bx, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copy in");
+  rc = launch_evaldiff(s, n_pts, dx, dv, dj, st);
+  if (rc != HT_OK) return rc;
+  e = cudaMemcpyAsync(val_host, dv, bv, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(jac_host, dj, bj, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copy out");
+  return HT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,51 @@
+// Host-side internals shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "ht.h"
+
+// The "instructions" of Table tabmemory: monomial supports and coefficients,
+// stored once on the device and read by all paths.
+struct ht_system {
+  int nv = 0, np = 0, limbs = 0, device = 0;
+  int64_t M = 0, n_pairs = 0;
+  int max_k = 0, max_exp = 0, max_deg = 0;
+  std::vector<int32_t> n_terms;  // host copies
+  std::vector<int8_t> exps;
+  std::vector<double> coef;
+  std::vector<int32_t> h_poly_off, h_mon_off;
+  std::vector<uint16_t> h_pairs;
+  void* d_block = nullptr;       // one device allocation holding the arrays below
+  int32_t* d_poly_off = nullptr; // [np + 1] monomial range of each polynomial
+  int32_t* d_mon_off = nullptr;  // [M + 1] range of each monomial in d_pairs
+  uint16_t* d_pairs = nullptr;   // variable | exponent << 8, variables increasing
+  double* d_coef = nullptr;      // [M][2][L]
+  void* d_ws = nullptr;          // workspace for the host-buffer entry points
+  size_t ws_bytes = 0;
+};
+
+namespace ht {
+
+int set_error(int code, const char* fmt, ...);
+int cuda_fail(cudaError_t e, const char* what);
+void clear_error();
+// True when p is device (or managed) memory of the current device.
+bool is_device_ptr(const void* p);
+int sm_count();
+
+template <int L>
+int launch_evaldiff_l(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st);
+inline int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac,
+                           cudaStream_t st) {
+  switch (s->limbs) {
+    case 1: return launch_evaldiff_l<1>(s, n_pts, x, val, jac, st);
+    case 2: return launch_evaldiff_l<2>(s, n_pts, x, val, jac, st);
+    case 4: return launch_evaldiff_l<4>(s, n_pts, x, val, jac, st);
+  }
+  return set_error(HT_EINVAL, "ht_eval_diff: limbs=%d", s->limbs);
+}
+
+}  // namespace ht

@@ -1,0 +1,156 @@
+"""Thin ctypes binding of the C ABI in include/ht.h (argument marshalling only).
+
+Each function has the name and argument order of its C counterpart.  Buffers
+may be torch tensors (their ``data_ptr()`` is passed), numpy arrays (host
+entry points only) or plain integer addresses.  A ``stream`` of None means
+torch's current CUDA stream.  A negative return code raises ``HTError`` with
+the library's message.  Every step of the computation runs in libht.so; if
+the library is missing every call raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libht.so")
+
+HT_D, HT_DD, HT_QD = 1, 2, 4
+HT_OK, HT_EINVAL, HT_ENOMEM, HT_ECUDA, HT_ETIMEOUT, HT_EUNSUPPORTED = 0, -1, -2, -3, -4, -5
+_ERR_NAMES = {-1: "HT_EINVAL", -2: "HT_ENOMEM", -3: "HT_ECUDA", -4: "HT_ETIMEOUT", -5: "HT_EUNSUPPORTED"}
+
+P = ctypes.c_void_p
+I32, I64 = ctypes.c_int, ctypes.c_int64
+
+# name -> (argtypes, restype); kept in the order of include/ht.h
+SIGNATURES = {
+    "ht_last_error": ([], ctypes.c_char_p),
+    "ht_create_system": ([I32, I32, P, P, P, I32, ctypes.POINTER(P)], I32),
+    "ht_destroy_system": ([P], I32),
+    "ht_system_info": ([P, P, P, P, P], I32),
+    "ht_eval_diff": ([P, I64, P, P, P, P], I32),
+    "ht_eval_diff_host": ([P, I64, P, P, P, P], I32),
+    "ht_bench_fp64_rate": ([I32, ctypes.POINTER(ctypes.c_double), P], I32),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HTError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s (%d): %s" % (_ERR_NAMES.get(code, "HT_E?"), code, msg))
+        self.code = code
+
+
+def lib() -> ctypes.CDLL:
+    """Load libht.so (built by paper_1505_00383_gb300._build)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError("libht.so is not built (%s); run `python -m paper_1505_00383_gb300._build` "
+                                   "or __graft_entry__.build()" % LIB_PATH)
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (args, res) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.argtypes = args
+                f.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(rc: int) -> int:
+    if rc < 0:
+        raise HTError(rc, lib().ht_last_error().decode())
+    return rc
+
+
+def _ptr(buf):
+    """Address of a torch tensor, numpy array or integer (None -> NULL)."""
+    if buf is None:
+        return None
+    if isinstance(buf, int):
+        return buf
+    if hasattr(buf, "data_ptr"):  # torch.Tensor
+        if not buf.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return buf.data_ptr()
+    if hasattr(buf, "ctypes"):  # numpy.ndarray
+        if not buf.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return buf.ctypes.data
+    raise TypeError("unsupported buffer type %r" % type(buf))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+class System:
+    """Owner of an ht_system handle; released by ht_destroy_system."""
+
+    def __init__(self, handle: int, n_vars: int, n_polys: int, limbs: int):
+        self.handle = handle
+        self.n_vars, self.n_polys, self.limbs = n_vars, n_polys, limbs
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ht_destroy_system(self.handle)
+            self.handle = None
+
+
+def ht_last_error() -> str:
+    return lib().ht_last_error().decode()
+
+
+def ht_create_system(n_vars, n_polys, n_terms, exps, coef, limbs) -> System:
+    """n_terms int32 [n_polys], exps int8 [M][n_vars], coef float64 [M][2][limbs] (host arrays)."""
+    import numpy as np
+    nt = np.ascontiguousarray(n_terms, dtype=np.int32)
+    ex = np.ascontiguousarray(exps, dtype=np.int8)
+    cf = np.ascontiguousarray(coef, dtype=np.float64)
+    out = P()
+    _check(lib().ht_create_system(n_vars, n_polys, _ptr(nt), _ptr(ex), _ptr(cf), limbs, ctypes.byref(out)))
+    return System(out.value, n_vars, n_polys, limbs)
+
+
+def ht_destroy_system(sys: System) -> None:
+    if sys.handle:
+        _check(lib().ht_destroy_system(sys.handle))
+        sys.handle = None
+
+
+def ht_system_info(sys: System):
+    nv, np_, L, M = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int64()
+    _check(lib().ht_system_info(sys.handle, ctypes.byref(nv), ctypes.byref(np_), ctypes.byref(L), ctypes.byref(M)))
+    return nv.value, np_.value, L.value, M.value
+
+
+def ht_eval_diff(sys: System, n_pts: int, x, val, jac, stream=None) -> None:
+    """Device buffers: x [nv][2][L][n_pts], val [np][2][L][n_pts], jac [np][nv][2][L][n_pts]."""
+    _check(lib().ht_eval_diff(sys.handle, n_pts, _ptr(x), _ptr(val), _ptr(jac), _stream(stream)))
+
+
+def ht_eval_diff_host(sys: System, n_pts: int, x, val, jac, stream=None) -> None:
+    """As ht_eval_diff on host buffers; returns when the results are in host memory."""
+    _check(lib().ht_eval_diff_host(sys.handle, n_pts, _ptr(x), _ptr(val), _ptr(jac), _stream(stream)))
+
+
+def system_from(system, limbs: int) -> System:
+    """Upload a synth.System-like object (n_vars, n_polys, n_terms, exps, coef_limbs)."""
+    return ht_create_system(system.n_vars, system.n_polys, system.n_terms, system.exps,
+                            system.coef_limbs(limbs), limbs)
+
+
+def ht_bench_fp64_rate(iters: int = 50, stream=None) -> float:
+    """Measured FP64 instructions per second of the current device."""
+    r = ctypes.c_double()
+    _check(lib().ht_bench_fp64_rate(iters, ctypes.byref(r), _stream(stream)))
+    return r.value

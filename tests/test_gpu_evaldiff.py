@@ -1,0 +1,121 @@
+"""Parity of the CUDA evaluation kernel (ht_eval_diff) with the oracle.
+
+Tolerance: relative 1e-12 (D), 1e-26 (DD), 1e-55 (QD), relative to the sum of
+the moduli of each output's terms (condition-aware: a plain |value| scale
+would punish the cancellation every random system has)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from parity import TOL, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ht():
+    from paper_1505_00383_gb300 import _build, ht as binding
+    _build.build()
+    oracle.build()
+    assert torch.cuda.is_available()
+    return binding
+
+
+def _run(ht, system, x, L, host=False):
+    nv, _, _, n = x.shape
+    hs = ht.system_from(system, L)
+    if host:
+        val = np.empty((system.n_polys, 2, L, n))
+        jac = np.empty((system.n_polys, nv, 2, L, n))
+        ht.ht_eval_diff_host(hs, n, np.ascontiguousarray(x), val, jac)
+        return val, jac
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    val = torch.full((system.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    jac = torch.full((system.n_polys, nv, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    ht.ht_eval_diff(hs, n, xd, val, jac)
+    torch.cuda.synchronize()
+    return val.cpu().numpy(), jac.cpu().numpy()
+
+
+def _check(system, x, L, val, jac, pts=None):
+    ov, oj = oracle.eval_(system, x, pts=pts)
+    mv, mj = oracle.eval_magnitude(system, x, pts=pts)
+    if pts is not None:
+        val, jac = val[..., pts], jac[..., pts]
+    assert np.all(np.isfinite(val)) and np.all(np.isfinite(jac))
+    ev, ej = rel_err(val, ov, mv), rel_err(jac, oj, mj)
+    assert ev <= TOL[L] and ej <= TOL[L], (L, ev, ej)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("name", ["c0_plain_d", "c2_batched_dd", "c4_stress_qd", "c1_evaldiff"])
+def test_evaldiff_matches_oracle_several_tiles_and_ragged_tail(ht, name, L):
+    s = synth.config_system(name)
+    n = 32 * 3 + 5  # three full warps of points and a ragged tail of 5
+    if name == "c1_evaldiff" and L == 4:
+        n = 32 + 3
+    x = synth.unit_points(101 + L, s.n_vars, n, L)
+    val, jac = _run(ht, s, x, L)
+    _check(s, x, L, val, jac)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_evaldiff_full_size_sampled(ht, L):
+    """The 65,536-point sweep in the launch configuration the benchmark times,
+    checked on sampled points (first, last, and random ones)."""
+    s = synth.config_system("c1_evaldiff")
+    n = 65536
+    x = synth.unit_points(1000 + L, s.n_vars, n, L)
+    val, jac = _run(ht, s, x, L)
+    rng = synth.SplitMix64(9 + L)
+    pts = np.unique(np.concatenate([[0, 31, 32, n - 1], rng.integers(0, n - 1, {1: 12, 2: 6, 4: 2}[L])]))
+    _check(s, x, L, val, jac, pts=pts)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_edge_cases_wide_supports_constants_high_degree(ht, L):
+    """A constant term, a monomial on 12 variables (the runtime-bounded path),
+    exponents up to 9, a single point."""
+    nv = 12
+    exps = np.zeros((5, nv), np.int8)
+    exps[1, :] = 1                       # all 12 variables
+    exps[2, 3] = 9                       # x3^9
+    exps[3, [0, 5, 11]] = [2, 3, 1]
+    exps[4, 7] = 1
+    coef = np.array([[0.5, -0.25], [1.0, 0.0], [-0.3, 0.7], [0.2, 0.2], [0.0, 1.0]])
+    s = synth.System(nv, 2, np.array([3, 2], np.int32), exps, coef)
+    for n in (1, 40):
+        x = synth.unit_points(7, nv, n, L)
+        val, jac = _run(ht, s, x, L)
+        _check(s, x, L, val, jac)
+
+
+def test_zero_points_is_a_noop_and_bad_args_are_rejected(ht):
+    s = synth.config_system("c0_plain_d")
+    hs = ht.system_from(s, 1)
+    x = torch.zeros((6, 2, 1, 4), dtype=torch.float64, device="cuda")
+    val = torch.zeros((6, 2, 1, 4), dtype=torch.float64, device="cuda")
+    jac = torch.zeros((6, 6, 2, 1, 4), dtype=torch.float64, device="cuda")
+    ht.ht_eval_diff(hs, 0, x, val, jac)
+    with pytest.raises(ht.HTError) as e:
+        ht.ht_eval_diff(hs, 4, x.cpu(), val, jac)  # host pointer for a device argument
+    assert e.value.code == ht.HT_EINVAL
+    with pytest.raises(ht.HTError):
+        ht.ht_eval_diff(hs, -1, x, val, jac)
+    with pytest.raises(ht.HTError):
+        ht.ht_eval_diff(hs, 4, x, x, jac)  # overlapping input and output
+    with pytest.raises(ht.HTError):
+        ht.ht_create_system(0, 1, [1], np.zeros((1, 0), np.int8), np.zeros((1, 2, 1)), 1)
+    with pytest.raises(ht.HTError):
+        ht.ht_create_system(2, 1, [1], np.zeros((1, 2), np.int8), np.zeros((1, 2, 3)), 3)
+
+
+@pytest.mark.parametrize("L", [1, 4])
+def test_host_buffer_entry_point_matches(ht, L):
+    s = synth.config_system("c2_batched_dd")
+    x = synth.unit_points(55, s.n_vars, 70, L)
+    v1, j1 = _run(ht, s, x, L)
+    v2, j2 = _run(ht, s, x, L, host=True)
+    assert np.array_equal(v1, v2) and np.array_equal(j1, j2)
