@@ -107,6 +107,106 @@ int ht_eval_diff(const ht_system* sys, int64_t n_pts, const double* x, double* v
 int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, double* val_host,
                       double* jac_host, void* stream);
 
+/* ---------------------------------------------------------------- tracking */
+
+/* Parameters of the predictor-corrector loop (Section 2 leaves every value
+ * open; ht_default_params gives this library's defaults). */
+typedef struct ht_params {
+  double h0;          /* first step size in t */
+  double h_min;       /* a path fails when a rejection takes the step below this */
+  double h_max;       /* largest step size */
+  double f_up;        /* step growth after an accepted step (>= 1) */
+  double f_down;      /* step shrink after a rejected step (0 < f_down < 1) */
+  double tol_dx;      /* corrector converged: |dx|_inf <= tol_dx max(1, |x|_inf) ... */
+  double tol_res;     /* ... and |h|_inf <= tol_res max(1, |x|_inf)^deg (deg: largest degree) */
+  double tol_polish;  /* Newton at t = 1 stops when |dx|_inf <= tol_polish max(1, |x|_inf) */
+  double r_div;       /* an accepted point with |x|_inf > r_div ends the path as diverged */
+  int32_t newton_max; /* evaluate-correct rounds per step (1..100) */
+  int32_t polish_max; /* Newton steps at t = 1 (0..100) */
+  int32_t max_steps;  /* steps (accepted + rejected) before a path fails */
+  int32_t max_order;  /* predictor order: extrapolation through up to max_order + 1 points (0..7) */
+  int32_t team_warps;       /* warps serving one group of 32 paths (1..8); 0 = chosen per round */
+  int32_t iters_per_launch; /* Newton steps per kernel launch; 0 = default (4) */
+  int32_t rounds_per_sync;  /* launches between host reads of the active count, even; 0 = default (8) */
+} ht_params;
+
+/* Counts of one ht_track_paths call. */
+typedef struct ht_stats {
+  int64_t converged, failed, diverged; /* final status 1, -1, -2 */
+  int64_t steps, rejects, newton;      /* totals over all paths */
+  int32_t launches;                    /* kernel launches (tracking + compaction) */
+  int32_t syncs;                       /* host reads of the active count */
+  double ms;                           /* wall time of the call */
+} ht_stats;
+
+/* Defaults for `limbs` (HT_D, HT_DD, HT_QD): h0 0.05, h_min 1e-5, h_max 0.1,
+ * f_up 1.5, f_down 0.5, tol_dx 1e-6, tol_res 1e-4, tol_polish 1e-12 / 1e-24 /
+ * 1e-48, r_div 1e8, newton_max 3, polish_max 4, max_steps 2000, max_order 4. */
+int ht_default_params(int limbs, ht_params* p);
+
+/*
+ * ht_start_solutions -- start points of the total-degree start system
+ * g_i = x_i^d_i - 1 (Eq. eqlinhom): path q gets x_i = exp(2 pi i k_i / d_i)
+ * with (k_0, k_1, ...) the mixed-radix digits of first + q, k_0 fastest, so the
+ * d_0 d_1 ... d_{n-1} paths (the Bezout number) are numbered 0.. without gaps.
+ *   degrees host [n], each >= 1;  x0 device [n][2][limbs][count].
+ * Blocks until the points are written.
+ */
+int ht_start_solutions(int n, const int32_t* degrees, int limbs, int64_t first, int64_t count, double* x0,
+                       void* stream);
+
+/*
+ * ht_mgs_solve -- least squares min |A x - b| for n_sys independent complex
+ * systems by modified Gram-Schmidt on the augmented matrix [A | b] followed by
+ * back substitution (the corrector's linear solve, Section 1 and Table
+ * tabmemory "correct").
+ *   Ab  device [rows][cols + 1][2][limbs][n_sys]: A then b as the last column;
+ *       overwritten with Q
+ *   R   device [cols][cols + 1][2][limbs][n_sys]: workspace, receives R (its
+ *       diagonal holds 1 / r_qq)
+ *   x   device [cols][2][limbs][n_sys]
+ * rows >= cols >= 1.  A rank-deficient system gives non-finite x.  Async.
+ */
+int ht_mgs_solve(int limbs, int rows, int cols, int64_t n_sys, double* Ab, double* R, double* x, void* stream);
+
+/*
+ * ht_compact -- the scan of Table tabjobidx: path_idx receives, in increasing
+ * order, the indices i < m with status[i] == 0, and *count their number.
+ *   status device [m] (int8), path_idx device [m] (int32), count device [1].
+ * m < 2^31.  Blocks until done.
+ */
+int ht_compact(const int8_t* status, int64_t m, int32_t* path_idx, int32_t* count, void* stream);
+
+/*
+ * ht_track_paths -- track n_paths solution paths of
+ *     gamma (1 - t) g(x) + t f(x) = 0,   g_i(x) = x_i^start_deg[i] - 1,
+ * from t = 0 to t = 1 (Eq. eqlinhom, Section 2): per step an extrapolation
+ * predictor through the current and up to max_order previous points, then up
+ * to newton_max evaluate-correct rounds (Newton with least squares by modified
+ * Gram-Schmidt), then step-size control; converged paths are refined by Newton
+ * at t = 1.  Status per path (Section 2, plus a reason code for failures):
+ * 1 success, -1 failure (step below h_min, too many steps, non-finite point),
+ * -2 diverged (|x|_inf > r_div).
+ *   f          square system (n_polys == n_vars == n) of the chosen precision;
+ *              the call keeps a workspace and CUDA graphs in it
+ *   start_deg  host [n], 1..64
+ *   gamma      host [2]: the random complex constant (re, im), nonzero
+ *   first_path paths first_path .. first_path + n_paths - 1 of the start
+ *              system when x0 is NULL (see ht_start_solutions)
+ *   x0         device [n][2][L][n_paths] start points, or NULL
+ *   p          parameters, or NULL for ht_default_params(L)
+ *   x_end      device [n][2][L][n_paths]: last accepted point of each path
+ *   status     device [n_paths] (int8)
+ *   t_end      device [n_paths]: t of the last accepted point
+ *   steps      device [n_paths] (int32) steps per path, or NULL
+ *   stats      host, or NULL
+ * Blocks until every path has finished.  HT_ETIMEOUT if paths are still
+ * active after the step limit allows (a bug guard).
+ */
+int ht_track_paths(ht_system* f, const int32_t* start_deg, const double* gamma, int64_t n_paths, int64_t first_path,
+                   const double* x0, const ht_params* p, double* x_end, int8_t* status, double* t_end,
+                   int32_t* steps, ht_stats* stats, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -66,6 +66,11 @@ def lib():
                 "hto_start_solutions": ([i32, i32, P, i64, i64, P], i32),
                 "hto_compact": ([P, i64, P, P], i64),
                 "hto_track": ([i32, i32, P, P, P, P, P, i64, P, P, i32, P, P, P, P, P, P], i32),
+                "hto_mlp_nparam": ([], i32),
+                "hto_mlp_forward": ([i64, P, P, P], i32),
+                "hto_mlp_loss_grad": ([i64, P, P, P, P], ctypes.c_double),
+                "hto_adam_step": ([i64, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, i32], i32),
             }
             for name, (args, res) in sig.items():
                 f = getattr(L, name)
@@ -210,3 +215,38 @@ def track(system, start_degrees, gamma, path_ids, limbs: int, params: dict | Non
                          _p(out["rejects"]), _p(out["newton"]))
     assert rc == 0
     return out
+
+
+# ------------------------------------------------------------------ learned step
+MLP_IN, MLP_HID, MLP_OUT = 16, 64, 2
+
+
+def mlp_nparam() -> int:
+    return lib().hto_mlp_nparam()
+
+
+def mlp_forward(x: np.ndarray, params: np.ndarray) -> np.ndarray:
+    """x [B][16] -> y [B][2] with the fp64 MLP (16 -> 64 -> 64 -> 2, ReLU)."""
+    x = _c(x, np.float64)
+    p = _c(params, np.float64)
+    y = np.empty((x.shape[0], MLP_OUT))
+    lib().hto_mlp_forward(x.shape[0], _p(x), _p(p), _p(y))
+    return y
+
+
+def mlp_loss_grad(x, target, params):
+    """(mean squared error, gradient over the flat parameters)."""
+    x = _c(x, np.float64)
+    t = _c(target, np.float64)
+    p = _c(params, np.float64)
+    g = np.empty(p.size)
+    loss = lib().hto_mlp_loss_grad(x.shape[0], _p(x), _p(t), _p(p), _p(g))
+    return float(loss), g
+
+
+def adam_step(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1):
+    """In place on p, m, v (float64 arrays)."""
+    for a in (p, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    gg = _c(g, np.float64)
+    lib().hto_adam_step(p.size, _p(p), _p(gg), _p(m), _p(v), lr, b1, b2, eps, step)

@@ -267,7 +267,7 @@ inline R<L> cabs2(const C<L>& a) {
 }
 template <int L>
 inline double cabs_d(const C<L>& a) {  // modulus from the leading limbs, in double
-  return std::hypot(a.re.v[0], a.im.v[0]);
+  return std::sqrt(a.re.v[0] * a.re.v[0] + a.im.v[0] * a.im.v[0]);
 }
 template <int L>
 inline bool cfinite(const C<L>& a) {
@@ -684,7 +684,9 @@ PathResult track_one(const Homotopy<L>& H, const double* P, std::vector<C<L>>& x
       ++res.newton;
       if (!(ndx == ndx)) break;  // NaN: reject
       double sx = std::max(1.0, norm_inf<L>(xp.data(), n));
-      if (ndx <= tol_dx * sx && nres <= tol_res * std::pow(sx, (double)H.deg_max)) {
+      double lim = tol_res;  // tol_res * sx^deg_max
+      for (int e = 0; e < H.deg_max; ++e) lim *= sx;
+      if (ndx <= tol_dx * sx && nres <= lim) {
         ok = true;
         break;
       }
@@ -723,6 +725,39 @@ PathResult track_one(const Homotopy<L>& H, const double* P, std::vector<C<L>>& x
   }
   res.t = t;
   return res;
+}
+
+
+// ---------------------------------------------------------- learned step MLP
+// Three dense layers 16 -> 64 -> 64 -> 2 with ReLU between them, fp64.
+// Parameters flat: W1[64][16] b1[64] W2[64][64] b2[64] W3[2][64] b3[2].
+constexpr int MI = 16, MH = 64, MO = 2;
+constexpr int MLP_NPARAM = MH * MI + MH + MH * MH + MH + MO * MH + MO;
+
+struct MlpView {
+  const double *W1, *b1, *W2, *b2, *W3, *b3;
+  explicit MlpView(const double* p)
+      : W1(p), b1(p + MH * MI), W2(b1 + MH), b2(W2 + MH * MH), W3(b2 + MH), b3(W3 + MO * MH) {}
+};
+
+void mlp_forward_one(const MlpView& w, const double* x, double* z1, double* h1, double* z2, double* h2, double* y) {
+  for (int o = 0; o < MH; ++o) {
+    double a = w.b1[o];
+    for (int i = 0; i < MI; ++i) a += w.W1[o * MI + i] * x[i];
+    z1[o] = a;
+    h1[o] = a > 0 ? a : 0;
+  }
+  for (int o = 0; o < MH; ++o) {
+    double a = w.b2[o];
+    for (int i = 0; i < MH; ++i) a += w.W2[o * MH + i] * h1[i];
+    z2[o] = a;
+    h2[o] = a > 0 ? a : 0;
+  }
+  for (int o = 0; o < MO; ++o) {
+    double a = w.b3[o];
+    for (int i = 0; i < MH; ++i) a += w.W3[o * MH + i] * h2[i];
+    y[o] = a;
+  }
 }
 
 template <typename F>
@@ -987,6 +1022,72 @@ int hto_track(int L, int n, const int32_t* n_terms, const int8_t* exps, const do
               int32_t* rejects, int32_t* newton) {
   return dispatch_l<TrackF>(L, n, n_terms, exps, coef, start_deg, gamma, n_paths, path_ids, params, n_threads,
                             x_end, status, t_end, steps, rejects, newton);
+}
+
+
+int hto_mlp_nparam(void) { return MLP_NPARAM; }
+
+// y[b][2] = MLP(x[b][16]) for b < B.
+int hto_mlp_forward(int64_t B, const double* x, const double* params, double* y) {
+  MlpView w(params);
+  double z1[MH], h1[MH], z2[MH], h2[MH];
+  for (int64_t b = 0; b < B; ++b) mlp_forward_one(w, x + b * MI, z1, h1, z2, h2, y + b * MO);
+  return 0;
+}
+
+// Mean squared error L = (1/B) sum_b sum_o (y_bo - t_bo)^2 and its gradient
+// with respect to every parameter (reverse mode through the three layers).
+double hto_mlp_loss_grad(int64_t B, const double* x, const double* target, const double* params, double* grad) {
+  MlpView w(params);
+  std::memset(grad, 0, sizeof(double) * MLP_NPARAM);
+  double *gW1 = grad, *gb1 = gW1 + MH * MI, *gW2 = gb1 + MH, *gb2 = gW2 + MH * MH, *gW3 = gb2 + MH,
+         *gb3 = gW3 + MO * MH;
+  double loss = 0;
+  double z1[MH], h1[MH], z2[MH], h2[MH], y[MO], dy[MO], dh2[MH], dz2[MH], dh1[MH], dz1[MH];
+  for (int64_t b = 0; b < B; ++b) {
+    const double* xb = x + b * MI;
+    mlp_forward_one(w, xb, z1, h1, z2, h2, y);
+    for (int o = 0; o < MO; ++o) {
+      double e = y[o] - target[b * MO + o];
+      loss += e * e;
+      dy[o] = 2.0 * e / (double)B;
+    }
+    for (int i = 0; i < MH; ++i) dh2[i] = 0;
+    for (int o = 0; o < MO; ++o) {
+      gb3[o] += dy[o];
+      for (int i = 0; i < MH; ++i) {
+        gW3[o * MH + i] += dy[o] * h2[i];
+        dh2[i] += dy[o] * w.W3[o * MH + i];
+      }
+    }
+    for (int i = 0; i < MH; ++i) dz2[i] = z2[i] > 0 ? dh2[i] : 0;
+    for (int i = 0; i < MH; ++i) dh1[i] = 0;
+    for (int o = 0; o < MH; ++o) {
+      gb2[o] += dz2[o];
+      for (int i = 0; i < MH; ++i) {
+        gW2[o * MH + i] += dz2[o] * h1[i];
+        dh1[i] += dz2[o] * w.W2[o * MH + i];
+      }
+    }
+    for (int i = 0; i < MH; ++i) dz1[i] = z1[i] > 0 ? dh1[i] : 0;
+    for (int o = 0; o < MH; ++o) {
+      gb1[o] += dz1[o];
+      for (int i = 0; i < MI; ++i) gW1[o * MI + i] += dz1[o] * xb[i];
+    }
+  }
+  return loss / (double)B;
+}
+
+// One Adam step (Kingma & Ba 2015) on fp64 parameters; step is 1-based.
+int hto_adam_step(int64_t n, double* p, const double* g, double* m, double* v, double lr, double b1, double b2,
+                  double eps, int step) {
+  double c1 = 1.0 - std::pow(b1, step), c2 = 1.0 - std::pow(b2, step);
+  for (int64_t i = 0; i < n; ++i) {
+    m[i] = b1 * m[i] + (1.0 - b1) * g[i];
+    v[i] = b2 * v[i] + (1.0 - b2) * g[i] * g[i];
+    p[i] -= lr * (m[i] / c1) / (std::sqrt(v[i] / c2) + eps);
+  }
+  return 0;
 }
 
 }  // extern "C"

@@ -27,6 +27,10 @@ UNITS = [
     ("ht_evaldiff.cu", ["-DHT_LIMBS=1"], "ht_evaldiff_1.o"),
     ("ht_evaldiff.cu", ["-DHT_LIMBS=2"], "ht_evaldiff_2.o"),
     ("ht_evaldiff.cu", ["-DHT_LIMBS=4"], "ht_evaldiff_4.o"),
+    ("ht_track.cu", ["-DHT_LIMBS=1"], "ht_track_1.o"),
+    ("ht_track.cu", ["-DHT_LIMBS=2"], "ht_track_2.o"),
+    ("ht_track.cu", ["-DHT_LIMBS=4"], "ht_track_4.o"),
+    ("ht_track_host.cu", [], "ht_track_host.o"),
 ]
 
 

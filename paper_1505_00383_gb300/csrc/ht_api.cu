@@ -145,6 +145,10 @@ int ht_destroy_system(ht_system* s) {
   cudaDeviceSynchronize();
   if (s->d_block) cudaFree(s->d_block);
   if (s->d_ws) cudaFree(s->d_ws);
+  if (s->d_track_ws) cudaFree(s->d_track_ws);
+  if (s->h_count) cudaFreeHost(s->h_count);
+  for (auto& g : s->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   delete s;
   return HT_OK;
 }

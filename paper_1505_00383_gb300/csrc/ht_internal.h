@@ -25,6 +25,17 @@ struct ht_system {
   double* d_coef = nullptr;      // [M][2][L]
   void* d_ws = nullptr;          // workspace for the host-buffer entry points
   size_t ws_bytes = 0;
+  void* d_track_ws = nullptr;    // per-path tracker state (grown on demand)
+  size_t track_ws_bytes = 0;
+  int32_t* h_count = nullptr;    // pinned host word: active paths after a round
+  struct GraphEntry {            // captured rounds of the tracker for one team size
+    int team = 0;
+    int64_t groups = 0;
+    const void* key_a = nullptr;
+    const void* key_b = nullptr;
+    cudaGraphExec_t exec = nullptr;
+  };
+  std::vector<GraphEntry> graphs;
 };
 
 namespace ht {

@@ -326,6 +326,104 @@ __device__ __forceinline__ cx<4> cmul(cx<4> a, cx<4> b) {
 __device__ __forceinline__ cx<4> cscale(cx<4> a, double s) { return cx<4>{qd_mul_d(a.re, s), qd_mul_d(a.im, s)}; }
 __device__ __forceinline__ cx<4> caxpy(cx<4> acc, double e, cx<4> d) { return cadd(acc, cscale(d, e)); }
 
+// ------------------------------------------------------------ L-limb reals
+template <int L>
+struct rtype;
+template <>
+struct rtype<1> {
+  using t = double;
+};
+template <>
+struct rtype<2> {
+  using t = dd;
+};
+template <>
+struct rtype<4> {
+  using t = qd;
+};
+template <int L>
+using rl = typename rtype<L>::t;
+
+__device__ __forceinline__ double r_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double r_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double r_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double r_div(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ double r_sqrt(double a) { return __dsqrt_rn(a); }
+__device__ __forceinline__ dd r_add(dd a, dd b) { return dd_add(a, b); }
+__device__ __forceinline__ dd r_sub(dd a, dd b) { return dd_sub(a, b); }
+__device__ __forceinline__ dd r_mul(dd a, dd b) { return dd_mul(a, b); }
+__device__ __forceinline__ dd r_div(dd a, dd b) { return dd_div(a, b); }
+__device__ __forceinline__ dd r_sqrt(dd a) { return dd_sqrt(a); }
+__device__ __forceinline__ qd r_add(qd a, qd b) { return qd_add(a, b); }
+__device__ __forceinline__ qd r_sub(qd a, qd b) { return qd_sub(a, b); }
+__device__ __forceinline__ qd r_mul(qd a, qd b) { return qd_mul(a, b); }
+__device__ __forceinline__ qd r_div(qd a, qd b) { return qd_div(a, b); }
+__device__ __forceinline__ qd r_sqrt(qd a) { return qd_sqrt(a); }
+template <int L>
+__device__ __forceinline__ rl<L> r_from(double d);
+template <>
+__device__ __forceinline__ double r_from<1>(double d) { return d; }
+template <>
+__device__ __forceinline__ dd r_from<2>(double d) { return dd{d, 0.0}; }
+template <>
+__device__ __forceinline__ qd r_from<4>(double d) { return qd_from(d); }
+// a - b for two doubles, in L-limb precision (exact for L >= 2)
+template <int L>
+__device__ __forceinline__ rl<L> r_diff(double a, double b) {
+  if constexpr (L == 1) {
+    return __dsub_rn(a, b);
+  } else {
+    double s, e;
+    two_sum(a, -b, s, e);
+    if constexpr (L == 2) {
+      return dd{s, e};
+    } else {
+      return qd{{s, e, 0.0, 0.0}};
+    }
+  }
+}
+__device__ __forceinline__ bool r_finite(double a) { return isfinite(a); }
+__device__ __forceinline__ bool r_finite(dd a) { return isfinite(a.hi) && isfinite(a.lo); }
+__device__ __forceinline__ bool r_finite(qd a) {
+  return isfinite(a.x[0]) && isfinite(a.x[1]) && isfinite(a.x[2]) && isfinite(a.x[3]);
+}
+
+// ------------------------------------------------------------ complex helpers
+// |a|^2, conj(a) * b and a * s (s an L-limb real), one rounding per component.
+__device__ __forceinline__ double cabs2(cx<1> a) { return __fma_rn(a.re, a.re, __dmul_rn(a.im, a.im)); }
+__device__ __forceinline__ dd cabs2(cx<2> a) { return dd_dot2(a.re, a.re, a.im, a.im); }
+__device__ __forceinline__ qd cabs2(cx<4> a) {
+  qd x[2] = {a.re, a.im};
+  const double s[2] = {1.0, 1.0};
+  return qd_dot<2>(x, x, s);
+}
+__device__ __forceinline__ cx<1> cconjmul(cx<1> a, cx<1> b) {
+  return cx<1>{__fma_rn(a.re, b.re, __dmul_rn(a.im, b.im)), __fma_rn(a.re, b.im, -__dmul_rn(a.im, b.re))};
+}
+__device__ __forceinline__ cx<2> cconjmul(cx<2> a, cx<2> b) {
+  return cx<2>{dd_dot2(a.re, b.re, a.im, b.im), dd_dot2(a.re, b.im, dd_neg(a.im), b.re)};
+}
+__device__ __forceinline__ cx<4> cconjmul(cx<4> a, cx<4> b) {
+  qd x1[2] = {a.re, a.im}, y1[2] = {b.re, b.im};
+  const double s1[2] = {1.0, 1.0};
+  qd x2[2] = {a.re, a.im}, y2[2] = {b.im, b.re};
+  const double s2[2] = {1.0, -1.0};
+  return cx<4>{qd_dot<2>(x1, y1, s1), qd_dot<2>(x2, y2, s2)};
+}
+__device__ __forceinline__ cx<1> cscale_r(cx<1> a, double s) { return cscale(a, s); }
+__device__ __forceinline__ cx<2> cscale_r(cx<2> a, dd s) { return cx<2>{dd_mul(a.re, s), dd_mul(a.im, s)}; }
+__device__ __forceinline__ cx<4> cscale_r(cx<4> a, qd s) { return cx<4>{qd_mul(a.re, s), qd_mul(a.im, s)}; }
+// Modulus from the leading limbs in double (used for norms and tests only).
+template <int L>
+__device__ __forceinline__ double cabs_lead(cx<L> a) {
+  double r = lead(a.re), i = lead(a.im);
+  return __dsqrt_rn(__dadd_rn(__dmul_rn(r, r), __dmul_rn(i, i)));
+}
+template <int L>
+__device__ __forceinline__ bool cfinite(cx<L> a) {
+  return r_finite(a.re) && r_finite(a.im);
+}
+
 // ------------------------------------------------------------ SoA access
 // A point batch is [count][2][L][n] doubles: plane (i, c, l) holds component
 // c (0 re, 1 im), limb l of entry i for all n points, point index fastest.

@@ -1,0 +1,493 @@
+// Many-path predictor-corrector tracking of gamma (1 - t) g(x) + t f(x) = 0
+// (Section 2 of Verschelde & Yu 2015), with g_i = x_i^d_i - 1.
+//
+// Execution model.  A CTA serves a group of 32 paths (one per lane) with T
+// warps; warp r is "team member" r for all 32 paths.  Every warp executes the
+// same instruction stream for its 32 paths (the SIMT picture of Table
+// tabsimtprecor), and the work of one Newton step is split over the T warps:
+//   * evaluation: warp r evaluates the polynomials j = r, r + T, ...;
+//   * modified Gram-Schmidt: warp r owns the columns j = r, r + T, ... of the
+//     augmented matrix [J | -h]; the owner of column q normalises it, then
+//     every warp projects its later columns (no cross-warp reductions: each
+//     dot product runs down a whole column in one warp);
+//   * prediction and the Newton update: warp r owns coordinates r, r + T, ...
+// One kernel launch runs `iters` Newton steps of every path of its groups; a
+// path's step (predict, 1..newton_max evaluate-correct rounds, accept or
+// reject, step-size control) is a small state machine advanced once per Newton
+// step, so lanes never wait for a predictor they do not need.  Between
+// launches the active paths are compacted by the scan of Table tabjobidx;
+// only the active count reaches the host.
+//
+// Per-path state lives in device memory in the vertical layout of Section 3
+// ([entry][2][L][m], path index fastest) -- the "work space for multiple
+// paths" of Table tabmemory.
+#include "ht_eval.cuh"
+#include "ht_internal.h"
+#include "ht_track.h"
+
+namespace ht {
+
+enum : int8_t { PH_TRACK = 0, PH_POLISH = 1 };
+
+// max over values that lets a NaN through (a NaN norm rejects the step)
+__device__ __forceinline__ double nanmax(double m, double v) { return (v > m || v != v) ? v : m; }
+
+template <int L>
+__device__ __forceinline__ cx<L> root_of_unity(int d, int k) {
+  if (d == 1 || k == 0) return creal<L>(1.0);
+  if (2 * k == d) return creal<L>(-1.0);
+  cx<L> z = czero<L>();
+  if (4 * k == d) {
+    z.im = r_from<L>(1.0);
+    return z;
+  }
+  if (4 * k == 3 * d) {
+    z.im = r_from<L>(-1.0);
+    return z;
+  }
+  double th = 2.0 * 3.14159265358979323846 * (double)k / (double)d;
+  double c, s;
+  sincos(th, &s, &c);
+  z.re = r_from<L>(c);
+  z.im = r_from<L>(s);
+  if constexpr (L > 1) {
+    // Newton on z^d - 1: z <- z - (z^d - 1) / (d z^(d-1))
+    for (int it = 0; it < 3; ++it) {
+      cx<L> zd1 = creal<L>(1.0);
+      for (int e = 0; e < d - 1; ++e) zd1 = cmul(zd1, z);
+      cx<L> f = csub(cmul(zd1, z), creal<L>(1.0));
+      cx<L> fp = cscale(zd1, (double)d);
+      rl<L> den = cabs2(fp);
+      cx<L> num = cconjmul(fp, f);
+      rl<L> inv = r_div(r_from<L>(1.0), den);
+      z = csub(z, cscale_r(num, inv));
+    }
+  }
+  return z;
+}
+
+// Path q's start point: mixed-radix digits of first + q, variable 0 fastest.
+template <int L>
+__global__ void start_kernel(int n, const int32_t* __restrict__ deg, int64_t first, int64_t count,
+                             double* __restrict__ x) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < count; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = first + q;
+    for (int i = 0; i < n; ++i) {
+      int d = __ldg(deg + i);
+      int k = (int)(r % d);
+      r /= d;
+      st<L>(x, i, count, q, root_of_unity<L>(d, k));
+    }
+  }
+}
+
+template <int L>
+__global__ void init_kernel(TrackArgs a) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.m; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int i = 0; i < a.n; ++i) st<L>(a.hx, i, a.m, p, ld<L>(a.x, i, a.m, p));
+    a.ht[p] = 0.0;
+    a.t[p] = 0.0;
+    a.h[p] = a.prm.h0;
+    a.t1[p] = 0.0;
+    a.status[p] = 0;
+    a.it[p] = 0;
+    a.phase[p] = PH_TRACK;
+    a.nh[p] = 1;
+    a.steps[p] = 0;
+    a.rejects[p] = 0;
+    a.newton[p] = 0;
+    a.idx0[p] = (int32_t)p;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.count0 = (int32_t)a.m;
+}
+
+// Modified Gram-Schmidt least squares on the augmented matrix [A | b] of one
+// path per lane (rows >= cols), columns dealt to the T warps of the CTA:
+// for q: r_qq = |a_q|, q_q = a_q / r_qq; for j > q: r_qj = q_q^H a_j,
+// a_j -= r_qj q_q; then back substitution R x = Q^H b.  A is
+// [rows][cols + 1][2][L][m], R is [cols][cols + 1][2][L][m] (R[q][q] holds
+// 1 / r_qq), x is [cols][2][L][m].  Every thread of the CTA must call this
+// (it contains barriers); lanes with act == false only take the barriers.
+template <int L>
+__device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
+                         int warp, int T) {
+  const int W = cols + 1;
+  rl<L> nrm_next = r_from<L>(0.0);
+  if (warp == 0 && act) {
+    rl<L> s = r_from<L>(0.0);
+    for (int i = 0; i < rows; ++i) s = r_add(s, cabs2(ld<L>(A, (int64_t)i * W, m, p)));
+    nrm_next = s;
+  }
+  for (int q = 0; q < cols; ++q) {
+    if (warp == q % T && act) {
+      rl<L> rqq = r_sqrt(nrm_next);
+      rl<L> inv = r_div(r_from<L>(1.0), rqq);
+      for (int i = 0; i < rows; ++i) {
+        int64_t e = (int64_t)i * W + q;
+        st<L>(A, e, m, p, cscale_r(ld<L>(A, e, m, p), inv));
+      }
+      cx<L> rv = czero<L>();
+      rv.re = inv;
+      st<L>(R, (int64_t)q * W + q, m, p, rv);
+    }
+    __syncthreads();
+    int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
+    for (int j = j0; j <= cols; j += T) {
+      if (!act) continue;
+      cx<L> r = czero<L>();
+      for (int i = 0; i < rows; ++i)
+        r = cadd(r, cconjmul(ld<L>(A, (int64_t)i * W + q, m, p), ld<L>(A, (int64_t)i * W + j, m, p)));
+      st<L>(R, (int64_t)q * W + j, m, p, r);
+      rl<L> s = r_from<L>(0.0);
+      for (int i = 0; i < rows; ++i) {
+        int64_t e = (int64_t)i * W + j;
+        cx<L> v = csub(ld<L>(A, e, m, p), cmul(r, ld<L>(A, (int64_t)i * W + q, m, p)));
+        st<L>(A, e, m, p, v);
+        if (j == q + 1) s = r_add(s, cabs2(v));
+      }
+      if (j == q + 1) nrm_next = s;  // the owner of column q + 1 normalises it next
+    }
+    __syncthreads();
+  }
+  if (warp == 0 && act) {
+    for (int q = cols - 1; q >= 0; --q) {
+      cx<L> acc = ld<L>(R, (int64_t)q * W + cols, m, p);
+      for (int j = q + 1; j < cols; ++j) acc = csub(acc, cmul(ld<L>(R, (int64_t)q * W + j, m, p), ld<L>(x, j, m, p)));
+      st<L>(x, q, m, p, cscale_r(acc, ld<L>(R, (int64_t)q * W + q, m, p).re));
+    }
+  }
+  __syncthreads();
+}
+
+// Standalone batched least squares (one system per lane, one warp per CTA).
+template <int L>
+__global__ void __launch_bounds__(32) mgs_kernel(double* A, double* R, double* x, int rows, int cols, int64_t n_sys) {
+  int64_t p = (int64_t)blockIdx.x * 32 + threadIdx.x;
+  mgs_team<L>(A, R, x, rows, cols, n_sys, p, p < n_sys, 0, 1);
+}
+
+// One Newton step (plus the bookkeeping around it) for `iters` rounds.
+template <int L>
+__global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
+  __shared__ double red[4][8][32];  // per-warp partials: residual, update, point norms; finiteness
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, T = blockDim.x >> 5;
+  const int n = a.n, W = n + 1;
+  const int64_t m = a.m;
+  const int count = *a.count_in;
+  const int64_t rowA = (int64_t)W * 2 * L * m;  // doubles per row of A
+  PolyView v;
+  v.mon_off = a.mon_off;
+  v.pairs = a.pairs;
+  v.coef = a.coef;
+  v.x = a.xp;
+  v.npts = m;
+  const cx<L> gamma = [&] {
+    cx<L> g = czero<L>();
+    g.re = r_from<L>(a.gamma_re);
+    g.im = r_from<L>(a.gamma_im);
+    return g;
+  }();
+  for (int64_t g = blockIdx.x; g * 32 < count; g += gridDim.x) {
+    const int64_t slot = g * 32 + lane;
+    const int64_t p = slot < count ? a.idx_in[slot] : -1;
+    for (int iter = 0; iter < a.iters; ++iter) {
+      int8_t stt = p >= 0 ? a.status[p] : (int8_t)1;
+      const bool act = stt == 0;
+      const int8_t ph = act ? a.phase[p] : (int8_t)0;
+      int it = act ? a.it[p] : 0;
+      double t = act ? a.t[p] : 0.0, h = act ? a.h[p] : 0.0, t1 = act ? a.t1[p] : 0.0;
+      int nh = act ? a.nh[p] : 1;
+      // ---- A: predictor (first Newton round of a step) or polish copy
+      if (act && ph == PH_TRACK && it == 0) {
+        double step = fmin(h, 1.0 - t);
+        t1 = (step >= 1.0 - t) ? 1.0 : t + step;
+        const int mm = min(nh, a.prm.max_order + 1);
+        const int base = nh - mm;
+        rl<L> w[8];
+        for (int j = 0; j < mm; ++j) {
+          rl<L> num = r_from<L>(1.0), den = r_from<L>(1.0);
+          double tj = a.ht[(int64_t)(base + j) * m + p];
+          for (int i = 0; i < mm; ++i) {
+            if (i == j) continue;
+            double ti = a.ht[(int64_t)(base + i) * m + p];
+            num = r_mul(num, r_diff<L>(t1, ti));
+            den = r_mul(den, r_diff<L>(tj, ti));
+          }
+          w[j] = r_div(num, den);
+        }
+        for (int i = warp; i < n; i += T) {
+          cx<L> acc = czero<L>();
+          for (int j = 0; j < mm; ++j)
+            acc = cadd(acc, cscale_r(ld<L>(a.hx, (int64_t)(base + j) * n + i, m, p), w[j]));
+          st<L>(a.xp, i, m, p, acc);
+        }
+      } else if (act && ph == PH_POLISH) {
+        for (int i = warp; i < n; i += T) st<L>(a.xp, i, m, p, ld<L>(a.x, i, m, p));
+      }
+      const double tt = (ph == PH_POLISH) ? 1.0 : t1;
+      __syncthreads();
+      // ---- B: h(x, tt) = gamma (1 - tt) (x_j^d_j - 1) + tt f_j(x), Jacobian rows
+      double pres = 0.0;
+      if (act) {
+        cx<L> gs = cscale_r(gamma, r_diff<L>(1.0, tt));
+        for (int j = warp; j < n; j += T) {
+          double* Arow = a.A + (int64_t)j * rowA;
+          cx<L> fj = eval_poly<L>(v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), n, p, Arow);
+          for (int i = 0; i < n; ++i) st<L>(Arow, i, m, p, cscale(ld<L>(Arow, i, m, p), tt));
+          const int d = __ldg(a.deg + j);
+          cx<L> xj = ld<L>(a.xp, j, m, p);
+          cx<L> xd1 = creal<L>(1.0);
+          for (int e = 0; e < d - 1; ++e) xd1 = cmul(xd1, xj);
+          cx<L> gval = csub(cmul(xd1, xj), creal<L>(1.0));
+          cx<L> hj = cadd(cmul(gs, gval), cscale(fj, tt));
+          cx<L> dg = cmul(gs, cscale(xd1, (double)d));
+          st<L>(Arow, j, m, p, cadd(ld<L>(Arow, j, m, p), dg));
+          cx<L> mh = czero<L>();
+          mh = csub(mh, hj);
+          st<L>(Arow, n, m, p, mh);
+          pres = nanmax(pres, cfinite(hj) ? cabs_lead(hj) : __longlong_as_double(0x7ff8000000000000LL));
+        }
+      }
+      __syncthreads();
+      // ---- C: least squares J dx = -h by modified Gram-Schmidt
+      mgs_team<L>(a.A, a.R, a.dx, n, n, m, p, act, warp, T);
+      // ---- D: x <- x + dx on this warp's coordinates; partial norms
+      double pdx = 0.0, pxp = 0.0;
+      if (act) {
+        for (int i = warp; i < n; i += T) {
+          cx<L> d = ld<L>(a.dx, i, m, p);
+          cx<L> xn = cadd(ld<L>(a.xp, i, m, p), d);
+          st<L>(a.xp, i, m, p, xn);
+          pdx = nanmax(pdx, cfinite(d) ? cabs_lead(d) : __longlong_as_double(0x7ff8000000000000LL));
+          pxp = nanmax(pxp, cabs_lead(xn));
+        }
+      }
+      red[0][warp][lane] = pres;
+      red[1][warp][lane] = pdx;
+      red[2][warp][lane] = pxp;
+      __syncthreads();
+      double nres = 0.0, ndx = 0.0, nxp = 0.0;
+      for (int w = 0; w < T; ++w) {
+        nres = nanmax(nres, red[0][w][lane]);
+        ndx = nanmax(ndx, red[1][w][lane]);
+        nxp = nanmax(nxp, red[2][w][lane]);
+      }
+      // ---- E: the state machine of a step (identical in every warp)
+      bool accept_point = false;  // copy xp into x (and maybe history)
+      bool push_hist = false;
+      int newton = 0, steps = 0, rejects = 0;
+      if (act) {
+        newton = a.newton[p] + 1;
+        steps = a.steps[p];
+        rejects = a.rejects[p];
+        const bool nan = !(ndx == ndx);
+        if (ph == PH_TRACK) {
+          ++it;
+          bool ok = false;
+          if (!nan) {
+            double sx = fmax(1.0, nxp);
+            double lim = a.prm.tol_res;
+            for (int e = 0; e < a.prm.deg_max; ++e) lim = __dmul_rn(lim, sx);
+            ok = ndx <= a.prm.tol_dx * sx && nres <= lim;
+          }
+          if (ok || nan || it >= a.prm.newton_max) {  // the step ends here
+            ++steps;
+            it = 0;
+            if (ok) {
+              t = t1;
+              accept_point = true;
+              push_hist = true;
+              h = fmin(a.prm.h_max, a.prm.f_up * h);
+              if (nxp > a.prm.r_div) {
+                stt = -2;
+              } else if (t == 1.0) {
+                if (a.prm.polish_max > 0) {
+                  // polish at t = 1 in the following rounds
+                } else {
+                  stt = 1;
+                }
+              }
+            } else {
+              ++rejects;
+              h = a.prm.f_down * h;
+              if (h < a.prm.h_min) stt = -1;
+            }
+            if (stt == 0 && steps >= a.prm.max_steps && !(ok && t == 1.0)) stt = -1;
+          }
+        } else {  // polish round at t = 1
+          if (nan) {
+            stt = 2;  // finished: status decided below from x
+          } else {
+            accept_point = true;
+            ++it;
+            if (ndx <= a.prm.tol_polish * fmax(1.0, nxp) || it >= a.prm.polish_max) stt = 2;
+          }
+        }
+      }
+      // copy the point and push the history on this warp's coordinates
+      bool xfinite = true;
+      if (act && accept_point) {
+        const int cap = a.prm.max_order + 1;
+        for (int i = warp; i < n; i += T) {
+          cx<L> xv = ld<L>(a.xp, i, m, p);
+          st<L>(a.x, i, m, p, xv);
+          if (push_hist) {
+            if (nh < cap) {
+              st<L>(a.hx, (int64_t)nh * n + i, m, p, xv);
+            } else {
+              for (int s = 0; s + 1 < cap; ++s) st<L>(a.hx, (int64_t)s * n + i, m, p, ld<L>(a.hx, (int64_t)(s + 1) * n + i, m, p));
+              st<L>(a.hx, (int64_t)(cap - 1) * n + i, m, p, xv);
+            }
+          }
+        }
+      }
+      if (act && stt == 2) {
+        for (int i = warp; i < n; i += T) xfinite = xfinite && cfinite(ld<L>(a.x, i, m, p));
+      }
+      red[3][warp][lane] = xfinite ? 1.0 : 0.0;
+      __syncthreads();
+      if (act && stt == 2) {
+        bool allf = true;
+        for (int w = 0; w < T; ++w) allf = allf && red[3][w][lane] != 0.0;
+        stt = allf ? 1 : -1;
+      }
+      if (warp == 0 && act) {
+        int8_t phn = ph;
+        if (ph == PH_TRACK && push_hist && stt == 0 && t == 1.0) {
+          phn = PH_POLISH;
+          it = 0;
+        }
+        if (push_hist) {
+          const int cap = a.prm.max_order + 1;
+          if (nh < cap) {
+            a.ht[(int64_t)nh * m + p] = t;
+            ++nh;
+          } else {
+            for (int s = 0; s + 1 < cap; ++s) a.ht[(int64_t)s * m + p] = a.ht[(int64_t)(s + 1) * m + p];
+            a.ht[(int64_t)(cap - 1) * m + p] = t;
+          }
+        }
+        a.status[p] = stt;
+        a.phase[p] = phn;
+        a.it[p] = (int8_t)it;
+        a.t[p] = t;
+        a.h[p] = h;
+        a.t1[p] = t1;
+        a.nh[p] = (int8_t)nh;
+        a.steps[p] = steps;
+        a.rejects[p] = rejects;
+        a.newton[p] = newton;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+#if HT_LIMBS == 1
+// Table tabjobidx: the paths whose status is 0 keep their relative order;
+// one CTA, 1024 threads, warp ballots for the scan.
+__global__ void __launch_bounds__(1024) compact_kernel(const int32_t* __restrict__ idx_in,
+                                                       const int32_t* __restrict__ count_in,
+                                                       const int8_t* __restrict__ status, int32_t* __restrict__ idx_out,
+                                                       int32_t* __restrict__ count_out) {
+  __shared__ int wsum[32];
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = *count_in;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int start = 0; start < n; start += 1024) {
+    const int i = start + threadIdx.x;
+    int32_t id = i < n ? idx_in[i] : -1;
+    const bool keep = i < n && status[id] == 0;
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    if (lane == 0) wsum[warp] = __popc(bal);
+    __syncthreads();
+    if (warp == 0) {
+      int v = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      wsum[lane] = v;  // inclusive prefix over warps
+    }
+    __syncthreads();
+    const int before = (warp ? wsum[warp - 1] : 0) + __popc(bal & ((1u << lane) - 1u));
+    if (keep) idx_out[base + before] = id;
+    __syncthreads();
+    if (threadIdx.x == 0) base += wsum[31];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *count_out = base;
+}
+
+#endif
+
+// --------------------------------------------------------------- host side
+template <int L>
+int launch_start_l(int n, const int32_t* d_deg, int64_t first, int64_t count, double* x, cudaStream_t st) {
+  if (count == 0) return HT_OK;
+  int64_t blocks = (count + 127) / 128;
+  if (blocks > 4096) blocks = 4096;
+  start_kernel<L><<<(unsigned)blocks, 128, 0, st>>>(n, d_deg, first, count, x);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "start solutions launch");
+}
+
+template <int L>
+int launch_mgs_l(double* A, double* R, double* x, int rows, int cols, int64_t n_sys, cudaStream_t st) {
+  if (n_sys == 0) return HT_OK;
+  mgs_kernel<L><<<(unsigned)((n_sys + 31) / 32), 32, 0, st>>>(A, R, x, rows, cols, n_sys);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "mgs launch");
+}
+
+#if HT_LIMBS == 1
+int launch_compact(const int32_t* idx_in, const int32_t* count_in, const int8_t* status, int32_t* idx_out,
+                   int32_t* count_out, cudaStream_t st) {
+  compact_kernel<<<1, 1024, 0, st>>>(idx_in, count_in, status, idx_out, count_out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "compact launch");
+}
+#endif
+
+template <int L>
+int launch_init_l(const TrackArgs& a, cudaStream_t st) {
+  int64_t blocks = (a.m + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  if (blocks < 1) blocks = 1;
+  init_kernel<L><<<(unsigned)blocks, 256, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "init launch");
+}
+
+template <int L>
+int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_t st) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L>, 32 * team, 0);
+  if (per_sm < 1) per_sm = 1;
+  int64_t grid = (int64_t)sm_count() * per_sm;
+  if (grid > max_groups) grid = max_groups;
+  if (grid < 1) grid = 1;
+  track_kernel<L><<<(unsigned)grid, 32 * team, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "track launch");
+}
+
+template <int L>
+int track_occupancy_l(int team) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L>, 32 * team, 0);
+  return per_sm;
+}
+
+#ifndef HT_LIMBS
+#error "compile once per precision with -DHT_LIMBS=1, 2 or 4"
+#endif
+template int launch_start_l<HT_LIMBS>(int, const int32_t*, int64_t, int64_t, double*, cudaStream_t);
+template int launch_mgs_l<HT_LIMBS>(double*, double*, double*, int, int, int64_t, cudaStream_t);
+template int launch_init_l<HT_LIMBS>(const TrackArgs&, cudaStream_t);
+template int launch_track_l<HT_LIMBS>(const TrackArgs&, int, int64_t, cudaStream_t);
+template int track_occupancy_l<HT_LIMBS>(int);
+
+}  // namespace ht

@@ -1,0 +1,331 @@
+// Host driver of the many-path tracker and the standalone entry points for its
+// stages (start solutions, least squares, compaction).
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ht_internal.h"
+#include "ht_track.h"
+
+namespace ht {
+
+template <typename F>
+static int by_limbs(int L, F f) {
+  switch (L) {
+    case 1: return f(std::integral_constant<int, 1>());
+    case 2: return f(std::integral_constant<int, 2>());
+    case 4: return f(std::integral_constant<int, 4>());
+  }
+  return set_error(HT_EINVAL, "limbs=%d must be 1, 2 or 4", L);
+}
+
+static size_t up256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Grow the system's tracker workspace to `bytes` (device) and make sure the
+// pinned host word for the active count exists.
+static int ensure_track_ws(ht_system* s, size_t bytes, cudaStream_t st) {
+  if (s->track_ws_bytes < bytes) {
+    if (s->d_track_ws) {
+      cudaStreamSynchronize(st);
+      cudaFree(s->d_track_ws);
+      s->d_track_ws = nullptr;
+      s->track_ws_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&s->d_track_ws, bytes);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(HT_ENOMEM, "ht_track_paths: workspace of %zu bytes", bytes);
+    }
+    s->track_ws_bytes = bytes;
+  }
+  if (!s->h_count) {
+    cudaError_t e = cudaHostAlloc((void**)&s->h_count, 2 * sizeof(int32_t), cudaHostAllocDefault);
+    if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: pinned count");
+  }
+  return HT_OK;
+}
+
+static void drop_graphs(ht_system* s) {
+  for (auto& g : s->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  s->graphs.clear();
+}
+
+}  // namespace ht
+
+using namespace ht;
+
+extern "C" {
+
+int ht_default_params(int limbs, ht_params* p) {
+  clear_error();
+  if (!p) return set_error(HT_EINVAL, "ht_default_params: NULL");
+  if (limbs != 1 && limbs != 2 && limbs != 4) return set_error(HT_EINVAL, "ht_default_params: limbs=%d", limbs);
+  std::memset(p, 0, sizeof *p);
+  p->h0 = 0.05;
+  p->h_min = 1e-5;
+  p->h_max = 0.1;
+  p->f_up = 1.5;
+  p->f_down = 0.5;
+  p->tol_dx = 1e-6;
+  p->tol_res = 1e-4;
+  p->tol_polish = limbs == 1 ? 1e-12 : (limbs == 2 ? 1e-24 : 1e-48);
+  p->r_div = 1e8;
+  p->newton_max = 3;
+  p->polish_max = 4;
+  p->max_steps = 2000;
+  p->max_order = 4;
+  return HT_OK;
+}
+
+int ht_start_solutions(int n, const int32_t* degrees, int limbs, int64_t first, int64_t count, double* x0,
+                       void* stream) {
+  clear_error();
+  if (n < 1 || !degrees || first < 0 || count < 0) return set_error(HT_EINVAL, "ht_start_solutions: bad arguments");
+  for (int i = 0; i < n; ++i)
+    if (degrees[i] < 1) return set_error(HT_EINVAL, "ht_start_solutions: degree %d of variable %d", degrees[i], i);
+  if (count == 0) return HT_OK;
+  if (!x0 || ((uintptr_t)x0 & 7) || !is_device_ptr(x0))
+    return set_error(HT_EINVAL, "ht_start_solutions: x0 must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  int32_t* d_deg = nullptr;
+  cudaError_t e = cudaMallocAsync(&d_deg, n * sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_start_solutions: alloc");
+  e = cudaMemcpyAsync(d_deg, degrees, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  int rc = e == cudaSuccess ? by_limbs(limbs, [&](auto c) { return launch_start_l<decltype(c)::value>(n, d_deg, first, count, x0, st); })
+                            : cuda_fail(e, "ht_start_solutions: copy");
+  cudaFreeAsync(d_deg, st);
+  if (rc == HT_OK) {
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ht_start_solutions");
+  }
+  return rc;
+}
+
+int ht_mgs_solve(int limbs, int rows, int cols, int64_t n_sys, double* Ab, double* R, double* x, void* stream) {
+  clear_error();
+  if (rows < 1 || cols < 1 || rows < cols || n_sys < 0)
+    return set_error(HT_EINVAL, "ht_mgs_solve: need rows >= cols >= 1, n_sys >= 0");
+  if (n_sys == 0) return HT_OK;
+  if (!Ab || !R || !x || (((uintptr_t)Ab | (uintptr_t)R | (uintptr_t)x) & 7) || !is_device_ptr(Ab) ||
+      !is_device_ptr(R) || !is_device_ptr(x))
+    return set_error(HT_EINVAL, "ht_mgs_solve: buffers must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  return by_limbs(limbs, [&](auto c) { return launch_mgs_l<decltype(c)::value>(Ab, R, x, rows, cols, n_sys, st); });
+}
+
+int ht_compact(const int8_t* status, int64_t m, int32_t* path_idx, int32_t* count, void* stream) {
+  clear_error();
+  if (m < 0 || m > 0x7fffffff) return set_error(HT_EINVAL, "ht_compact: m=%lld", (long long)m);
+  if (!count || !is_device_ptr(count) || (m > 0 && (!status || !path_idx || !is_device_ptr(status) ||
+                                                     !is_device_ptr(path_idx))))
+    return set_error(HT_EINVAL, "ht_compact: buffers must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  // identity index list in a temporary buffer, then the stable compaction
+  int32_t* tmp = nullptr;
+  cudaError_t e = cudaMallocAsync(&tmp, (m + 1) * sizeof(int32_t), st);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_compact: alloc");
+  std::vector<int32_t> h(m + 1);
+  for (int64_t i = 0; i < m; ++i) h[i] = (int32_t)i;
+  h[m] = (int32_t)m;
+  e = cudaMemcpyAsync(tmp, h.data(), (m + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  int rc = e == cudaSuccess ? launch_compact(tmp, tmp + m, status, path_idx, count, st) : cuda_fail(e, "ht_compact");
+  if (rc == HT_OK) e = cudaStreamSynchronize(st);
+  cudaFreeAsync(tmp, st);
+  if (rc == HT_OK && e != cudaSuccess) rc = cuda_fail(e, "ht_compact");
+  return rc;
+}
+
+int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, int64_t n_paths, int64_t first_path,
+                   const double* x0, const ht_params* prm_in, double* x_end, int8_t* status, double* t_end,
+                   int32_t* steps, ht_stats* stats, void* stream) {
+  clear_error();
+  auto t_start = std::chrono::steady_clock::now();
+  if (!s) return set_error(HT_EINVAL, "ht_track_paths: NULL system");
+  if (s->np != s->nv) return set_error(HT_EINVAL, "ht_track_paths: system must be square (%d x %d)", s->np, s->nv);
+  const int n = s->nv, L = s->limbs;
+  if (!start_deg || !gamma) return set_error(HT_EINVAL, "ht_track_paths: NULL start_deg or gamma");
+  if (n_paths < 0 || n_paths > 0x7fffffff || first_path < 0)
+    return set_error(HT_EINVAL, "ht_track_paths: n_paths=%lld first_path=%lld", (long long)n_paths, (long long)first_path);
+  int deg_max = s->max_deg;
+  for (int i = 0; i < n; ++i) {
+    if (start_deg[i] < 1 || start_deg[i] > 64) return set_error(HT_EINVAL, "ht_track_paths: start degree %d", start_deg[i]);
+    if (start_deg[i] > deg_max) deg_max = start_deg[i];
+  }
+  if (!std::isfinite(gamma[0]) || !std::isfinite(gamma[1]) || (gamma[0] == 0.0 && gamma[1] == 0.0))
+    return set_error(HT_EINVAL, "ht_track_paths: gamma must be finite and nonzero");
+  ht_params P;
+  if (prm_in)
+    P = *prm_in;
+  else
+    ht_default_params(L, &P);
+  if (!(P.h0 > 0) || !(P.h_min > 0) || !(P.h_max >= P.h_min) || !(P.f_up >= 1) || !(P.f_down > 0 && P.f_down < 1) ||
+      P.newton_max < 1 || P.newton_max > 100 || P.polish_max < 0 || P.polish_max > 100 || P.max_steps < 1 ||
+      P.max_order < 0 || P.max_order > 7 || P.team_warps < 0 || P.team_warps > 8 || P.iters_per_launch < 0 ||
+      P.rounds_per_sync < 0 || (P.rounds_per_sync & 1) || !(P.tol_dx > 0) || !(P.tol_res > 0) || !(P.tol_polish > 0) || !(P.r_div > 0))
+    return set_error(HT_EINVAL, "ht_track_paths: invalid parameters");
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (n_paths == 0) return HT_OK;
+  if (!x_end || !status || !t_end || !is_device_ptr(x_end) || !is_device_ptr(status) || !is_device_ptr(t_end) ||
+      (x0 && !is_device_ptr(x0)) || (steps && !is_device_ptr(steps)) || (((uintptr_t)x_end | (uintptr_t)t_end) & 7))
+    return set_error(HT_EINVAL, "ht_track_paths: outputs (and x0) must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t m = n_paths;
+  const int cap = P.max_order + 1;
+  const size_t cxb = (size_t)2 * L * m * sizeof(double);  // one complex entry for all paths
+  // workspace layout
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    size_t o = off;
+    off += up256(b);
+    return o;
+  };
+  size_t o_xp = take(n * cxb), o_hx = take((size_t)cap * n * cxb), o_ht = take((size_t)cap * m * 8),
+         o_A = take((size_t)n * (n + 1) * cxb), o_R = take((size_t)n * (n + 1) * cxb), o_dx = take(n * cxb),
+         o_h = take(m * 8), o_t1 = take(m * 8), o_it = take(m), o_ph = take(m), o_nh = take(m),
+         o_steps = take(m * 4), o_rej = take(m * 4), o_newt = take(m * 4), o_idx0 = take((m + 1) * 4),
+         o_idx1 = take((m + 1) * 4), o_cnt = take(2 * 4), o_deg = take(n * 4);
+  int rc = ensure_track_ws(s, off, st);
+  if (rc != HT_OK) return rc;
+  char* w = (char*)s->d_track_ws;
+  TrackArgs a;
+  a.poly_off = s->d_poly_off;
+  a.mon_off = s->d_mon_off;
+  a.pairs = s->d_pairs;
+  a.coef = s->d_coef;
+  a.deg = (const int32_t*)(w + o_deg);
+  a.gamma_re = gamma[0];
+  a.gamma_im = gamma[1];
+  a.n = n;
+  a.m = m;
+  a.prm = TrackPrm{P.h0, P.h_min, P.h_max, P.f_up, P.f_down, P.tol_dx, P.tol_res, P.tol_polish, P.r_div,
+                   P.newton_max, P.polish_max, P.max_steps, P.max_order, deg_max};
+  a.x = x_end;
+  a.xp = (double*)(w + o_xp);
+  a.hx = (double*)(w + o_hx);
+  a.ht = (double*)(w + o_ht);
+  a.A = (double*)(w + o_A);
+  a.R = (double*)(w + o_R);
+  a.dx = (double*)(w + o_dx);
+  a.t = t_end;
+  a.h = (double*)(w + o_h);
+  a.t1 = (double*)(w + o_t1);
+  a.status = status;
+  a.it = (int8_t*)(w + o_it);
+  a.phase = (int8_t*)(w + o_ph);
+  a.nh = (int8_t*)(w + o_nh);
+  a.steps = steps ? steps : (int32_t*)(w + o_steps);
+  a.rejects = (int32_t*)(w + o_rej);
+  a.newton = (int32_t*)(w + o_newt);
+  int32_t* idx[2] = {(int32_t*)(w + o_idx0), (int32_t*)(w + o_idx1)};
+  int32_t* cnt[2] = {(int32_t*)(w + o_cnt), (int32_t*)(w + o_cnt) + 1};
+  a.idx0 = idx[0];
+  a.count0 = cnt[0];
+  cudaError_t e = cudaMemcpyAsync((void*)a.deg, start_deg, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: upload degrees");
+  if (x0) {
+    e = cudaMemcpyAsync(x_end, x0, n * cxb, cudaMemcpyDeviceToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: copy x0");
+  } else {
+    rc = by_limbs(L, [&](auto c) { return launch_start_l<decltype(c)::value>(n, a.deg, first_path, m, x_end, st); });
+    if (rc != HT_OK) return rc;
+  }
+  rc = by_limbs(L, [&](auto c) { return launch_init_l<decltype(c)::value>(a, st); });
+  if (rc != HT_OK) return rc;
+
+  // Rounds: [track (iters Newton steps) ; compact] x rounds_per_sync per host
+  // read of the active count, captured once per team size as a CUDA graph.
+  const int iters = P.iters_per_launch > 0 ? P.iters_per_launch : 4;
+  const int rounds = P.rounds_per_sync > 0 ? P.rounds_per_sync : 8;
+  const int sms = sm_count();
+  auto pick_team = [&](int64_t active) {
+    if (P.team_warps > 0) return P.team_warps;
+    int64_t groups = (active + 31) / 32;
+    int64_t target = (int64_t)sms * 8;  // two warps per SM sub-partition
+    int t = 1;
+    while (t < 8 && t < n && groups * t * 2 <= target) t *= 2;
+    return t;
+  };
+  int64_t active = m;
+  int64_t max_loops = (int64_t)P.max_steps * (P.newton_max + 1) + P.polish_max + 8;
+  int64_t loops = 0;
+  int launches = 0, syncs = 0;
+  drop_graphs(s);
+  while (active > 0) {
+    int team = pick_team(active);
+    int64_t groups = (active + 31) / 32;
+    // graph for this (team, iters, rounds, workspace, outputs) configuration
+    ht_system::GraphEntry* ge = nullptr;
+    for (auto& g : s->graphs)
+      if (g.team == team && g.key_a == (const void*)x_end && g.key_b == (const void*)status && g.groups >= groups) ge = &g;
+    if (!ge) {
+      cudaGraph_t graph;
+      cudaStream_t cs;
+      e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: capture stream");
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) {
+        cudaStreamDestroy(cs);
+        return cuda_fail(e, "ht_track_paths: begin capture");
+      }
+      int crc = HT_OK;
+      for (int r = 0; r < rounds && crc == HT_OK; ++r) {
+        TrackArgs ar = a;
+        ar.idx_in = idx[r & 1];
+        ar.count_in = cnt[r & 1];
+        ar.iters = iters;
+        crc = by_limbs(L, [&](auto c) { return launch_track_l<decltype(c)::value>(ar, team, groups, cs); });
+        if (crc == HT_OK) crc = launch_compact(idx[r & 1], cnt[r & 1], status, idx[(r + 1) & 1], cnt[(r + 1) & 1], cs);
+      }
+      cudaError_t ee = cudaStreamEndCapture(cs, &graph);
+      cudaStreamDestroy(cs);
+      if (crc != HT_OK) return crc;
+      if (ee != cudaSuccess) return cuda_fail(ee, "ht_track_paths: end capture");
+      ht_system::GraphEntry g;
+      g.team = team;
+      g.groups = groups;
+      g.key_a = x_end;
+      g.key_b = status;
+      ee = cudaGraphInstantiate(&g.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ee != cudaSuccess) return cuda_fail(ee, "ht_track_paths: instantiate");
+      s->graphs.push_back(g);
+      ge = &s->graphs.back();
+    }
+    e = cudaGraphLaunch(ge->exec, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: graph launch");
+    launches += 2 * rounds;
+    e = cudaMemcpyAsync(s->h_count, cnt[0], sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: read active count");
+    ++syncs;
+    active = s->h_count[0];
+    loops += (int64_t)rounds * iters;
+    if (loops > max_loops && active > 0) return set_error(HT_ETIMEOUT, "ht_track_paths: paths still active after %lld Newton rounds", (long long)loops);
+  }
+  if (stats) {
+    std::vector<int8_t> hs(m);
+    std::vector<int32_t> hst(m), hrj(m), hnw(m);
+    e = cudaMemcpyAsync(hs.data(), status, m, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hst.data(), a.steps, m * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hrj.data(), a.rejects, m * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hnw.data(), a.newton, m * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: stats");
+    for (int64_t q = 0; q < m; ++q) {
+      stats->converged += hs[q] == 1;
+      stats->failed += hs[q] == -1;
+      stats->diverged += hs[q] == -2;
+      stats->steps += hst[q];
+      stats->rejects += hrj[q];
+      stats->newton += hnw[q];
+    }
+    stats->launches = launches;
+    stats->syncs = syncs;
+    stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+  }
+  return HT_OK;
+}
+
+}  // extern "C"

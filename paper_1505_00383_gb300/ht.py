@@ -31,8 +31,30 @@ SIGNATURES = {
     "ht_system_info": ([P, P, P, P, P], I32),
     "ht_eval_diff": ([P, I64, P, P, P, P], I32),
     "ht_eval_diff_host": ([P, I64, P, P, P, P], I32),
+    "ht_default_params": ([I32, P], I32),
+    "ht_start_solutions": ([I32, P, I32, I64, I64, P, P], I32),
+    "ht_mgs_solve": ([I32, I32, I32, I64, P, P, P, P], I32),
+    "ht_compact": ([P, I64, P, P, P], I32),
+    "ht_track_paths": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P], I32),
     "ht_bench_fp64_rate": ([I32, ctypes.POINTER(ctypes.c_double), P], I32),
 }
+
+
+
+class ht_params(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("h0", "h_min", "h_max", "f_up", "f_down", "tol_dx", "tol_res",
+                                                "tol_polish", "r_div")] + \
+               [(k, ctypes.c_int32) for k in ("newton_max", "polish_max", "max_steps", "max_order", "team_warps",
+                                               "iters_per_launch", "rounds_per_sync")]
+
+
+class ht_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("converged", "failed", "diverged", "steps", "rejects", "newton")] + \
+               [("launches", ctypes.c_int32), ("syncs", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
 
 _lock = threading.Lock()
 _lib = None
@@ -154,3 +176,38 @@ def ht_bench_fp64_rate(iters: int = 50, stream=None) -> float:
     r = ctypes.c_double()
     _check(lib().ht_bench_fp64_rate(iters, ctypes.byref(r), _stream(stream)))
     return r.value
+
+
+def ht_default_params(limbs: int, **over) -> "ht_params":
+    p = ht_params()
+    _check(lib().ht_default_params(limbs, ctypes.byref(p)))
+    for k, v in over.items():
+        setattr(p, k, v)
+    return p
+
+
+def ht_start_solutions(n, degrees, limbs, first, count, x0, stream=None) -> None:
+    import numpy as np
+    d = np.ascontiguousarray(degrees, dtype=np.int32)
+    _check(lib().ht_start_solutions(n, _ptr(d), limbs, first, count, _ptr(x0), _stream(stream)))
+
+
+def ht_mgs_solve(limbs, rows, cols, n_sys, Ab, R, x, stream=None) -> None:
+    _check(lib().ht_mgs_solve(limbs, rows, cols, n_sys, _ptr(Ab), _ptr(R), _ptr(x), _stream(stream)))
+
+
+def ht_compact(status, m, path_idx, count, stream=None) -> None:
+    _check(lib().ht_compact(_ptr(status), m, _ptr(path_idx), _ptr(count), _stream(stream)))
+
+
+def ht_track_paths(sys: System, start_deg, gamma, n_paths, first_path, x0, params, x_end, status, t_end,
+                   steps=None, stats: "ht_stats | None" = None, stream=None) -> None:
+    """Track paths first_path.. of gamma (1 - t) g + t f = 0; device outputs
+    x_end [n][2][L][n_paths], status int8 [n_paths], t_end [n_paths]."""
+    import numpy as np
+    d = np.ascontiguousarray(start_deg, dtype=np.int32)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    pp = None if params is None else ctypes.byref(params)
+    sp = None if stats is None else ctypes.byref(stats)
+    _check(lib().ht_track_paths(sys.handle, _ptr(d), _ptr(g), n_paths, first_path, _ptr(x0), pp, _ptr(x_end),
+                                _ptr(status), _ptr(t_end), _ptr(steps), sp, _stream(stream)))

@@ -1,0 +1,236 @@
+"""Parity of the CUDA tracker stages and of whole-path tracking with the oracle."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from match import match_sets, to_complex
+from parity import TOL, cerr
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+@pytest.fixture(scope="module")
+def ht():
+    from paper_1505_00383_gb300 import _build, ht as binding
+    _build.build()
+    oracle.build()
+    assert torch.cuda.is_available()
+    return binding
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    return (t if dtype is None else t.to(dtype)).cuda()
+
+
+# ---------------------------------------------------------------- stages
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("degrees", [[2, 2, 2], [3, 2], [5, 3, 4]])
+def test_start_solutions_match_oracle(ht, L, degrees):
+    count = int(np.prod(degrees))
+    x = torch.full((len(degrees), 2, L, count), np.nan, dtype=torch.float64, device="cuda")
+    ht.ht_start_solutions(len(degrees), degrees, L, 0, count, x)
+    ref = oracle.start_solutions(degrees, 0, count, L)
+    e = cerr(x.cpu().numpy(), ref)
+    assert np.max(e) <= {1: 4e-16, 2: 1e-31, 4: 1e-62}[L], np.max(e)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("rows,cols", [(6, 6), (12, 12), (9, 5), (1, 1)])
+def test_mgs_solve_matches_oracle(ht, L, rows, cols):
+    rng = synth.SplitMix64(300 + rows * 7 + cols + L)
+    n_sys = 37  # a full warp of systems and a ragged tail
+    re, im = synth.unit_circle(rng, n_sys * rows * (cols + 1))
+    mag = rng.uniform(re.size) + 0.5
+    Ab = np.zeros((rows, cols + 1, 2, L, n_sys))
+    Ab[:, :, 0] = synth.random_tails(rng, (re * mag).reshape(rows, cols + 1, n_sys), L).transpose(1, 2, 0, 3)
+    Ab[:, :, 1] = synth.random_tails(rng, (im * mag).reshape(rows, cols + 1, n_sys), L).transpose(1, 2, 0, 3)
+    A_or = np.ascontiguousarray(Ab[:, :cols].transpose(4, 0, 1, 2, 3))
+    b_or = np.ascontiguousarray(Ab[:, cols].transpose(3, 0, 1, 2))
+    ref = oracle.mgs_solve(A_or, b_or)  # [n_sys][cols][2][L]
+    dAb = dev(Ab)
+    dR = torch.empty((cols, cols + 1, 2, L, n_sys), dtype=torch.float64, device="cuda")
+    dx = torch.empty((cols, 2, L, n_sys), dtype=torch.float64, device="cuda")
+    ht.ht_mgs_solve(L, rows, cols, n_sys, dAb, dR, dx)
+    torch.cuda.synchronize()
+    got = dx.cpu().numpy()
+    refv = np.ascontiguousarray(ref.transpose(1, 2, 3, 0))
+    for s in range(n_sys):
+        Ad = Ab[:, :cols, 0, 0, s] + 1j * Ab[:, :cols, 1, 0, s]
+        cond = np.linalg.cond(Ad)
+        scale = np.max(np.abs(refv[:, 0, 0, s] + 1j * refv[:, 1, 0, s]))
+        e = np.max(cerr(got[..., s:s + 1], refv[..., s:s + 1]))
+        assert e <= 64 * cond * cond * 2.0 ** (-53 * L) * scale * rows, (s, e, cond)
+
+
+def test_compaction_table_tabjobidx(ht):
+    g = json.load(open(os.path.join(GOLDEN, "tabjobidx.json")))
+    st = dev(np.array(g["status"], np.int8))
+    idx = torch.full((5,), -7, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    ht.ht_compact(st, 5, idx, cnt)
+    c = int(cnt.item())
+    assert c == g["active_count"]
+    assert idx[:c].cpu().tolist() == g["path_idx"]
+
+
+@pytest.mark.parametrize("m", [1, 31, 1024, 1025, 70000])
+def test_compaction_random_matches_oracle(ht, m):
+    rng = synth.SplitMix64(m)
+    st = (rng.integers(0, 3, m) - 1).astype(np.int8)
+    idx = torch.full((m,), -7, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros((1,), dtype=torch.int32, device="cuda")
+    ht.ht_compact(dev(st), m, idx, cnt)
+    _, ref = oracle.compact(st)
+    c = int(cnt.item())
+    assert c == ref.size and np.array_equal(idx[:c].cpu().numpy(), ref)
+
+
+# ---------------------------------------------------------------- tracking
+def _oracle_params(L, **over):
+    return oracle.default_params(L, **over)
+
+
+def _gpu_params(ht, L, **over):
+    return ht.ht_default_params(L, **over)
+
+
+def track_gpu(ht, system, L, m, first=0, start_deg=None, gamma=(0.6, 0.8), **over):
+    n = system.n_vars
+    deg = system.degrees() if start_deg is None else np.asarray(start_deg, np.int32)
+    hs = ht.system_from(system, L)
+    x = torch.full((n, 2, L, m), np.nan, dtype=torch.float64, device="cuda")
+    status = torch.full((m,), 9, dtype=torch.int8, device="cuda")
+    t = torch.full((m,), np.nan, dtype=torch.float64, device="cuda")
+    steps = torch.zeros((m,), dtype=torch.int32, device="cuda")
+    stats = ht.ht_stats()
+    ht.ht_track_paths(hs, deg, gamma, m, first, None, _gpu_params(ht, L, **over), x, status, t, steps, stats)
+    torch.cuda.synchronize()
+    return dict(x_end=x.cpu().numpy(), status=status.cpu().numpy(), t_end=t.cpu().numpy(),
+                steps=steps.cpu().numpy(), stats=stats.as_dict())
+
+
+def track_oracle(system, L, ids, start_deg=None, gamma=(0.6, 0.8), **over):
+    deg = system.degrees() if start_deg is None else np.asarray(start_deg, np.int32)
+    return oracle.track(system, deg, gamma, np.asarray(ids, np.int64), L, _oracle_params(L, **over))
+
+
+def assert_same_outcome(g, o, tol=1e-10):
+    """Equal counts of converged, failed and diverged paths; the converged
+    endpoints agree as sets to tol (relative to max(1, |x|))."""
+    for code in (1, -1, -2):
+        assert int(np.sum(g["status"] == code)) == int(np.sum(o["status"] == code)), (code, g["status"], o["status"])
+    conv_g = to_complex(g["x_end"])[g["status"] == 1]
+    conv_o = to_complex(o["x_end"])[o["status"] == 1]
+    ok, worst = match_sets(conv_g, conv_o, tol)
+    assert ok, worst
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_diagonal_system_closed_form(ht, L):
+    c = np.array([0.3 + 0.8j, -1.1 + 0.2j, 0.5 - 0.9j])
+    exps, coef = [], []
+    for i, ci in enumerate(c):
+        a = [0, 0, 0]
+        a[i] = 2
+        exps += [a, [0, 0, 0]]
+        coef += [[1.0, 0.0], [-ci.real, -ci.imag]]
+    s = synth.System(3, 3, np.full(3, 2, np.int32), np.array(exps, np.int8), np.array(coef))
+    g = track_gpu(ht, s, L, 8)
+    assert np.all(g["status"] == 1) and np.all(g["t_end"] == 1.0)
+    r = np.sqrt(c)
+    expect = np.array([[r[0] * (1 - 2 * ((p >> 0) & 1)), r[1] * (1 - 2 * ((p >> 1) & 1)),
+                        r[2] * (1 - 2 * ((p >> 2) & 1))] for p in range(8)])
+    ok, worst = match_sets(to_complex(g["x_end"]), expect, 1e-13)
+    assert ok, worst
+    o = track_oracle(s, L, np.arange(8))
+    assert_same_outcome(g, o)
+    # per path, the same endpoint as the oracle to working precision
+    e = cerr(g["x_end"], o["x_end"])
+    assert np.max(e) <= {1: 1e-13, 2: 1e-26, 4: 1e-50}[L]
+
+
+@pytest.mark.parametrize("h_min", [0.01, 1e-6])
+def test_plain_tracker_c0_matches_oracle(ht, h_min):
+    """64 paths of the n = 6 total-degree homotopy in complex double, with the
+    step range 0.01-0.1 of the workload and with a small step floor."""
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    g = track_gpu(ht, s, 1, 64, gamma=gam, h_min=h_min)
+    o = track_oracle(s, 1, np.arange(64), gamma=gam, h_min=h_min)
+    assert_same_outcome(g, o)
+    assert np.array_equal(g["status"], o["status"])
+    assert np.array_equal(g["steps"], o["steps"])
+    st = g["stats"]
+    assert st["converged"] == np.sum(o["status"] == 1) and st["steps"] == int(np.sum(o["steps"]))
+    assert st["newton"] == int(np.sum(o["newton"])) and st["rejects"] == int(np.sum(o["rejects"]))
+
+
+def test_team_size_and_launch_shape_do_not_change_results(ht):
+    """Every team size splits the same arithmetic differently over warps but
+    in the same order, so results are bitwise identical."""
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    base = track_gpu(ht, s, 1, 64, gamma=gam, team_warps=1, iters_per_launch=1, rounds_per_sync=2)
+    for tw, it, rs in ((2, 4, 8), (4, 3, 4), (8, 7, 6), (0, 0, 0)):
+        r = track_gpu(ht, s, 1, 64, gamma=gam, team_warps=tw, iters_per_launch=it, rounds_per_sync=rs)
+        for k in ("x_end", "status", "t_end", "steps"):
+            assert np.array_equal(r[k], base[k], equal_nan=True), (tw, it, rs, k)
+
+
+def test_sharded_path_ranges_union_equals_full_run(ht):
+    """Paths are independent (Section 1): tracking path ranges separately (as
+    separate GPUs would) gives the full run's results."""
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    full = track_gpu(ht, s, 1, 64, gamma=gam, h_min=1e-6)
+    parts = [track_gpu(ht, s, 1, 24, first=0, gamma=gam, h_min=1e-6),
+             track_gpu(ht, s, 1, 40, first=24, gamma=gam, h_min=1e-6)]
+    x = np.concatenate([p["x_end"] for p in parts], axis=-1)
+    st = np.concatenate([p["status"] for p in parts])
+    assert np.array_equal(x, full["x_end"]) and np.array_equal(st, full["status"])
+
+
+@pytest.mark.parametrize("name,L,m,sample", [("c2_batched_dd", 2, 4096, 48), ("c4_stress_qd", 4, 1024, 16)])
+def test_batched_tracker_sampled_paths_match_oracle(ht, name, L, m, sample):
+    """The batched tracker on the workload shape (all 4,096 DD paths; 1,024 of
+    the QD paths); a seeded sample of paths is re-tracked one by one by the
+    oracle and must end with the same status and endpoint."""
+    s = synth.config_system(name)
+    gam = synth.random_gamma(synth.CONFIGS[name]["seed"])
+    g = track_gpu(ht, s, L, m, gamma=gam, h_min=1e-6)
+    assert set(np.unique(g["status"])) <= {1, -1, -2}
+    assert g["stats"]["converged"] + g["stats"]["failed"] + g["stats"]["diverged"] == m
+    rng = synth.SplitMix64(7)
+    ids = np.unique(np.concatenate([[0, m - 1], rng.integers(0, m - 1, sample)]))
+    o = track_oracle(s, L, ids, gamma=gam, h_min=1e-6)
+    sub = dict(x_end=g["x_end"][..., ids], status=g["status"][ids])
+    assert np.array_equal(sub["status"], o["status"]), (sub["status"], o["status"])
+    conv = o["status"] == 1
+    e = cerr(sub["x_end"][..., conv], o["x_end"][..., conv])
+    scale = np.maximum(1.0, np.max(np.abs(to_complex(o["x_end"][..., conv])), axis=1))
+    assert np.all(np.max(e, axis=0) / scale <= 1e-10)
+
+
+def test_tracker_rejects_bad_arguments(ht):
+    s = synth.config_system("c0_plain_d")
+    hs = ht.system_from(s, 1)
+    x = torch.zeros((6, 2, 1, 4), dtype=torch.float64, device="cuda")
+    st = torch.zeros((4,), dtype=torch.int8, device="cuda")
+    t = torch.zeros((4,), dtype=torch.float64, device="cuda")
+    with pytest.raises(ht.HTError):  # zero gamma
+        ht.ht_track_paths(hs, [2] * 6, (0.0, 0.0), 4, 0, None, None, x, st, t)
+    with pytest.raises(ht.HTError):  # host output
+        ht.ht_track_paths(hs, [2] * 6, (1.0, 0.0), 4, 0, None, None, x.cpu(), st, t)
+    with pytest.raises(ht.HTError):  # odd rounds_per_sync
+        ht.ht_track_paths(hs, [2] * 6, (1.0, 0.0), 4, 0, None, ht.ht_default_params(1, rounds_per_sync=3), x, st, t)
+    with pytest.raises(ht.HTError):  # non-square system
+        rect = synth.System(6, 5, s.n_terms[:5], s.exps[:40], s.coef[:40])
+        ht.ht_track_paths(ht.system_from(rect, 1), [2] * 6, (1.0, 0.0), 4, 0, None, None, x, st, t)
+    ht.ht_track_paths(hs, [2] * 6, (1.0, 0.0), 0, 0, None, None, x, st, t)  # no paths: no-op
