@@ -207,6 +207,31 @@ int ht_track_paths(ht_system* f, const int32_t* start_deg, const double* gamma, 
                    const double* x0, const ht_params* p, double* x_end, int8_t* status, double* t_end,
                    int32_t* steps, ht_stats* stats, void* stream);
 
+/*
+ * ht_compact_noalloc -- ht_compact for callers that cannot allocate device
+ * memory.  The paper has no counterpart; this is an interface variant.
+ *
+ * Who needs it: code that runs where cudaMalloc and cudaFree are forbidden or
+ * harmful.  Examples are a host thread inside another framework's allocator
+ * (which must own every device allocation), a latency-critical loop that must
+ * not synchronise the device the way cudaFree can, or a caller with a fixed
+ * memory budget.  ht_compact allocates a temporary index list on every call;
+ * this variant instead uses a fixed array of HT_NOALLOC_MAX_PATHS + 1 int32
+ * (16 MiB) that the library declares at file scope.  Every GPU that loads the
+ * library holds that array until the process exits.
+ *
+ * Same arguments, result and blocking behaviour as ht_compact, except:
+ *   - m above HT_NOALLOC_MAX_PATHS is rejected with HT_EINVAL;
+ *   - no cudaMalloc, cudaFree or other allocating routine is called;
+ *   - the first call on a device looks up the array's device address with that
+ *     device current.  Make that first call before any stream capture;
+ *   - all calls share the one array, which keeps the last call's contents.
+ *     Each call rewrites all of it that it reads.  Calls whose work overlaps on
+ *     the GPU (other streams, other host threads) race on it, so serialise them.
+ */
+#define HT_NOALLOC_MAX_PATHS (1 << 22)
+int ht_compact_noalloc(const int8_t* status, int64_t m, int32_t* path_idx, int32_t* count, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,7 @@ SIGNATURES = {
     "ht_start_solutions": ([I32, P, I32, I64, I64, P, P], I32),
     "ht_mgs_solve": ([I32, I32, I32, I64, P, P, P, P], I32),
     "ht_compact": ([P, I64, P, P, P], I32),
+    "ht_compact_noalloc": ([P, I64, P, P, P], I32),
     "ht_track_paths": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P], I32),
     "ht_bench_fp64_rate": ([I32, ctypes.POINTER(ctypes.c_double), P], I32),
 }
@@ -198,6 +199,15 @@ def ht_mgs_solve(limbs, rows, cols, n_sys, Ab, R, x, stream=None) -> None:
 
 def ht_compact(status, m, path_idx, count, stream=None) -> None:
     _check(lib().ht_compact(_ptr(status), m, _ptr(path_idx), _ptr(count), _stream(stream)))
+
+
+HT_NOALLOC_MAX_PATHS = 1 << 22
+
+
+def ht_compact_noalloc(status, m, path_idx, count, stream=None) -> None:
+    """ht_compact without allocating: scratch is a fixed array in the library
+    (m <= HT_NOALLOC_MAX_PATHS)."""
+    _check(lib().ht_compact_noalloc(_ptr(status), m, _ptr(path_idx), _ptr(count), _stream(stream)))
 
 
 def ht_track_paths(sys: System, start_deg, gamma, n_paths, first_path, x0, params, x_end, status, t_end,
