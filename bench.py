@@ -73,6 +73,8 @@ def _args():
     p.add_argument("--n-pts", type=int, default=65536)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--track", default="c0_plain_d,c2_batched_dd",
+                   help="tracking workloads to time as well (comma list, '' for none)")
     return p.parse_args()
 
 
@@ -157,6 +159,42 @@ def cpu_oracle_rate(system, budget_pts, threads=0, seed=77):
     return 1.0 / per_pt
 
 
+TRACK_LIMBS = {"c0_plain_d": 1, "c2_batched_dd": 2, "c3_learned_d": 1, "c4_stress_qd": 4}
+
+
+def track_workload(ht, torch, name, rank, world, reps=2):
+    """paths/s of ht_track_paths on one tracking workload (all its paths on
+    every rank: weak scaling), with the final status counts."""
+    cfg = synth.CONFIGS[name]
+    L = TRACK_LIMBS[name]
+    system = synth.config_system(name)
+    deg = system.degrees()
+    m = int(np.prod(deg.astype(np.int64)))
+    gam = synth.random_gamma(cfg["seed"])
+    over = {"h_min": 0.01} if name == "c0_plain_d" else {"h_min": 1e-6}
+    prm = ht.ht_default_params(L, **over)
+    hs = ht.system_from(system, L)
+    n = system.n_vars
+    x = torch.empty((n, 2, L, m), dtype=torch.float64, device="cuda")
+    st = torch.empty((m,), dtype=torch.int8, device="cuda")
+    t = torch.empty((m,), dtype=torch.float64, device="cuda")
+    stats = ht.ht_stats()
+    ht.ht_track_paths(hs, deg, gam, m, 0, None, prm, x, st, t, None, stats)  # warm-up (graphs, workspace)
+    times = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ht.ht_track_paths(hs, deg, gam, m, 0, None, prm, x, st, t, None, stats)
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    sec = statistics.mean(times)
+    d = stats.as_dict()
+    return {"paths": m, "precision": NAMES[L], "n": n, "s": sec, "paths_per_s": world * m / sec,
+            "converged": d["converged"], "failed": d["failed"], "diverged": d["diverged"],
+            "steps_per_path": d["steps"] / m, "newton_per_path": d["newton"] / m, "launches": d["launches"],
+            "syncs": d["syncs"]}
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -208,6 +246,10 @@ def run_ours(a):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
     fp64_peak = ht.ht_bench_fp64_rate(100)
+    tuned = {}
+    for L in PRECISIONS:  # autotuner: kernel body and CTA size per precision (part of warm-up)
+        v, t, ms = ht.ht_tune_eval(sys_h[L], n, xs[L], vals[L], jacs[L], reps=1)
+        tuned[NAMES[L]] = {"variant": "compact" if v == 1 else "unrolled", "threads": t}
 
     def step(events=None):
         for L in PRECISIONS:
@@ -282,6 +324,10 @@ def run_ours(a):
         per_prec[NAMES[L]] = {"ms": m, "pts_per_s": n / (m * 1e-3), "fp64_frac": ops / (m * 1e-3) / fp64_peak,
                               "out_GB_per_s": (system.n_polys * (system.n_vars + 1) * 16 * L * n) / (m * 1e-3) / 1e9}
 
+    tracking = {}
+    for name in [w for w in a.track.split(",") if w]:
+        tracking[name] = track_workload(ht, torch, name, rank, world)
+
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
         cores = os.cpu_count() or 1
@@ -299,7 +345,7 @@ def run_ours(a):
                        "monomial_vars": "2-8", "exponents": "1-3", "n_pts_per_gpu": n,
                        "l2": "flushed (512 MB write) before every timed step; outputs 1.1-4.5 GB per launch",
                        "parallelism": "independent batch per GPU"},
-            "per_precision": per_prec, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "per_precision": per_prec, "tuned": tuned, "tracking": tracking, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": a.steps * len(PRECISIONS), "clocks": clk.summary(),
             "wall_s_timed_region": t_wall,
         }))

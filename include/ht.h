@@ -107,6 +107,27 @@ int ht_eval_diff(const ht_system* sys, int64_t n_pts, const double* x, double* v
 int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, double* val_host,
                       double* jac_host, void* stream);
 
+/* ------------------------------------------------------------ tuning */
+
+/*
+ * ht_set_eval_config -- choose how ht_eval_diff runs on this system:
+ *   variant  1 compact monomial bodies (one code path for every support size),
+ *            0 unrolled bodies for supports of up to 8 variables, -1 default (1)
+ *   threads  CTA size 64, 128 or 256, or 0 for the default (128)
+ * Both variants perform the same operations in the same order, so results do
+ * not depend on the choice; only the speed does.
+ */
+int ht_set_eval_config(ht_system* sys, int variant, int threads);
+
+/*
+ * ht_tune_eval -- autotuner for ht_eval_diff: times every (variant, threads)
+ * configuration on the given device buffers (reps timed launches each, CUDA
+ * events on `stream`), keeps the fastest in the system and reports it (any
+ * output pointer may be NULL).  Overwrites val and jac.  Blocks.
+ */
+int ht_tune_eval(ht_system* sys, int64_t n_pts, const double* x, double* val, double* jac, int reps, int* variant,
+                 int* threads, float* best_ms, void* stream);
+
 /* ---------------------------------------------------------------- tracking */
 
 /* Parameters of the predictor-corrector loop (Section 2 leaves every value

@@ -33,6 +33,15 @@ bool is_device_ptr(const void* p) {
   cudaGetDevice(&dev);
   return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
+int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st) {
+  switch (s->limbs) {
+    case 1: return launch_evaldiff_l<1>(s, n_pts, x, val, jac, st);
+    case 2: return launch_evaldiff_l<2>(s, n_pts, x, val, jac, st);
+    case 4: return launch_evaldiff_l<4>(s, n_pts, x, val, jac, st);
+  }
+  return set_error(HT_EINVAL, "ht_eval_diff: limbs=%d", s->limbs);
+}
+
 int sm_count() {
   int dev = 0, n = 0;
   cudaGetDevice(&dev);
@@ -227,6 +236,58 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
   if (e == cudaSuccess) e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copy out");
   return HT_OK;
+}
+
+int ht_set_eval_config(ht_system* s, int variant, int threads) {
+  clear_error();
+  if (!s) return set_error(HT_EINVAL, "ht_set_eval_config: NULL system");
+  if (variant < -1 || variant > 1) return set_error(HT_EINVAL, "ht_set_eval_config: variant=%d", variant);
+  if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
+    return set_error(HT_EINVAL, "ht_set_eval_config: threads=%d (0, 64, 128 or 256)", threads);
+  s->eval_variant = variant;
+  s->eval_threads = threads;
+  return HT_OK;
+}
+
+int ht_tune_eval(ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, int reps, int* variant,
+                 int* threads, float* best_ms, void* stream) {
+  clear_error();
+  int rc = check_eval_args(s, n_pts, x, val, jac, true);
+  if (rc != HT_OK) return rc;
+  if (n_pts == 0 || reps < 1) return set_error(HT_EINVAL, "ht_tune_eval: need n_pts > 0 and reps >= 1");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const int variants[2] = {1, 0}, sizes[3] = {128, 64, 256};
+  float best = 1e30f;
+  int bv = 1, bt = 128;
+  for (int vi = 0; vi < 2 && rc == HT_OK; ++vi)
+    for (int ti = 0; ti < 3 && rc == HT_OK; ++ti) {
+      s->eval_variant = variants[vi];
+      s->eval_threads = sizes[ti];
+      rc = launch_evaldiff(s, n_pts, x, val, jac, st);  // warm-up
+      cudaEventRecord(e0, st);
+      for (int r = 0; r < reps && rc == HT_OK; ++r) rc = launch_evaldiff(s, n_pts, x, val, jac, st);
+      cudaEventRecord(e1, st);
+      cudaError_t e = cudaEventSynchronize(e1);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+      if (e != cudaSuccess && rc == HT_OK) rc = cuda_fail(e, "ht_tune_eval");
+      if (rc == HT_OK && ms / reps < best) {
+        best = ms / reps;
+        bv = variants[vi];
+        bt = sizes[ti];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  s->eval_variant = bv;
+  s->eval_threads = bt;
+  if (variant) *variant = bv;
+  if (threads) *threads = bt;
+  if (best_ms) *best_ms = best;
+  return rc;
 }
 
 }  // extern "C"

@@ -26,6 +26,17 @@ struct PolyView {
   int64_t npts;             // column stride of x and of the Jacobian row
 };
 
+// J += e * d for a derivative d and its exponent e.  In complex double the fma
+// with e = 1 rounds exactly like the add, so no branch is taken there.
+template <int L>
+__device__ __forceinline__ cx<L> jacc(cx<L> J, double e, cx<L> d) {
+  if constexpr (L == 1) {
+    return caxpy(J, e, d);
+  } else {
+    return e == 1.0 ? cadd(J, d) : caxpy(J, e, d);
+  }
+}
+
 template <int L, int K>
 __device__ __forceinline__ void mono_fixed(const PolyView& a, int m, int64_t p, double* jrow, cx<L>& accv) {
   const uint16_t* pr = a.pairs + __ldg(a.mon_off + m);
@@ -52,27 +63,29 @@ __device__ __forceinline__ void mono_fixed(const PolyView& a, int m, int64_t p, 
   for (int r = 1; r < K; ++r) P[r] = cmul(P[r - 1], xs[r]);
   accv = cadd(accv, P[K - 1]);
   if constexpr (K == 1) {
-    J[0] = (ex[0] == 1.0) ? cadd(J[0], cf) : caxpy(J[0], ex[0], cf);
+    J[0] = jacc<L>(J[0], ex[0], cf);
   } else {
-    J[K - 1] = (ex[K - 1] == 1.0) ? cadd(J[K - 1], P[K - 2]) : caxpy(J[K - 1], ex[K - 1], P[K - 2]);
+    J[K - 1] = jacc<L>(J[K - 1], ex[K - 1], P[K - 2]);
     cx<L> S = xs[K - 1];
 #pragma unroll
     for (int r = K - 2; r >= 1; --r) {
       cx<L> d = cmul(P[r - 1], S);
-      J[r] = (ex[r] == 1.0) ? cadd(J[r], d) : caxpy(J[r], ex[r], d);
+      J[r] = jacc<L>(J[r], ex[r], d);
       S = cmul(S, xs[r]);
     }
     cx<L> d0 = cmul(cf, S);
-    J[0] = (ex[0] == 1.0) ? cadd(J[0], d0) : caxpy(J[0], ex[0], d0);
+    J[0] = jacc<L>(J[0], ex[0], d0);
   }
 #pragma unroll
   for (int r = 0; r < K; ++r) st<L>(jrow, var[r], a.npts, p, J[r]);
 }
 
-// Supports wider than 8 variables: the same sweep with runtime bounds (local
-// memory arrays); rare in practice.
+// The same sweep with runtime bounds: one compact body for every support size
+// (forward products in local memory).  It performs the operations of
+// mono_fixed in the same order, so both give bitwise identical results; the
+// compact body keeps the instruction cache warm when supports vary.
 template <int L>
-__device__ __noinline__ void mono_wide(const PolyView& a, int m, int64_t p, double* jrow, cx<L>& accv) {
+__device__ __noinline__ void mono_loop(const PolyView& a, int m, int64_t p, double* jrow, cx<L>& accv) {
   const int beg = __ldg(a.mon_off + m), k = __ldg(a.mon_off + m + 1) - beg;
   const uint16_t* pr = a.pairs + beg;
   cx<L> P[64];
@@ -87,27 +100,42 @@ __device__ __noinline__ void mono_wide(const PolyView& a, int m, int64_t p, doub
     P[r] = cmul(r == 0 ? cf : P[r - 1], xr);
   }
   accv = cadd(accv, P[k - 1]);
-  cx<L> S = creal<L>(1.0);
-  for (int r = k - 1; r >= 0; --r) {
-    uint16_t q = __ldg(pr + r);
-    int v = q & 0xff;
-    double e = (double)(q >> 8);
-    cx<L> d = (r == 0) ? cmul(cf, S) : cmul(P[r - 1], S);
-    cx<L> Jv = ld<L>(jrow, v, a.npts, p);
-    st<L>(jrow, v, a.npts, p, e == 1.0 ? cadd(Jv, d) : caxpy(Jv, e, d));
-    if (r > 0) S = cmul(S, ld<L>(a.x, v, a.npts, p));
+  if (k == 1) {
+    uint16_t q = __ldg(pr);
+    st<L>(jrow, q & 0xff, a.npts, p, jacc<L>(ld<L>(jrow, q & 0xff, a.npts, p), (double)(q >> 8), cf));
+    return;
   }
+  uint16_t q = __ldg(pr + k - 1);
+  int v = q & 0xff;
+  st<L>(jrow, v, a.npts, p, jacc<L>(ld<L>(jrow, v, a.npts, p), (double)(q >> 8), P[k - 2]));
+  cx<L> S = ld<L>(a.x, v, a.npts, p);
+  for (int r = k - 2; r >= 1; --r) {
+    q = __ldg(pr + r);
+    v = q & 0xff;
+    cx<L> d = cmul(P[r - 1], S);
+    st<L>(jrow, v, a.npts, p, jacc<L>(ld<L>(jrow, v, a.npts, p), (double)(q >> 8), d));
+    S = cmul(S, ld<L>(a.x, v, a.npts, p));
+  }
+  q = __ldg(pr);
+  v = q & 0xff;
+  cx<L> d0 = cmul(cf, S);
+  st<L>(jrow, v, a.npts, p, jacc<L>(ld<L>(jrow, v, a.npts, p), (double)(q >> 8), d0));
 }
-
 
 // Value of polynomial j (monomials m0..m1-1) at column p; its gradient is
 // accumulated into jrow ([nv][2][L][npts], zeroed here first).
-template <int L>
+// LOOP selects the compact body for every monomial; otherwise supports of up
+// to 8 variables use the unrolled bodies.
+template <int L, bool LOOP = true>
 __device__ __forceinline__ cx<L> eval_poly(const PolyView& a, int m0, int m1, int nv, int64_t p, double* jrow) {
   for (int i = 0; i < nv; ++i) st<L>(jrow, i, a.npts, p, czero<L>());
   cx<L> accv = czero<L>();
   for (int m = m0; m < m1; ++m) {
     const int k = __ldg(a.mon_off + m + 1) - __ldg(a.mon_off + m);
+    if (LOOP && k > 0) {
+      mono_loop<L>(a, m, p, jrow, accv);
+      continue;
+    }
     switch (k) {
       case 0: accv = cadd(accv, ld_coef<L>(a.coef + (int64_t)m * 2 * L)); break;
       case 1: mono_fixed<L, 1>(a, m, p, jrow, accv); break;
@@ -118,7 +146,7 @@ __device__ __forceinline__ cx<L> eval_poly(const PolyView& a, int m0, int m1, in
       case 6: mono_fixed<L, 6>(a, m, p, jrow, accv); break;
       case 7: mono_fixed<L, 7>(a, m, p, jrow, accv); break;
       case 8: mono_fixed<L, 8>(a, m, p, jrow, accv); break;
-      default: mono_wide<L>(a, m, p, jrow, accv); break;
+      default: mono_loop<L>(a, m, p, jrow, accv); break;
     }
   }
   return accv;

@@ -36,8 +36,8 @@ struct EvalArgs {
   int64_t n_units;
 };
 
-template <int L>
-__global__ void __launch_bounds__(128) evaldiff_kernel(EvalArgs a) {
+template <int L, bool LOOP>
+__global__ void __launch_bounds__(256) evaldiff_kernel(EvalArgs a) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -47,9 +47,24 @@ __global__ void __launch_bounds__(128) evaldiff_kernel(EvalArgs a) {
     const int j = (int)(u % a.np);
     const int64_t p = (u / a.np) * 32 + lane;
     if (p >= n) continue;  // lanes past the ragged tail sit the unit out
-    cx<L> v = eval_poly<L>(a.v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), a.nv, p, a.jac + (int64_t)j * plane);
+    cx<L> v = eval_poly<L, LOOP>(a.v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), a.nv, p, a.jac + (int64_t)j * plane);
     st<L>(a.val, j, n, p, v);
   }
+}
+
+template <int L, bool LOOP>
+static int launch_v(const EvalArgs& a, int threads, cudaStream_t st) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaldiff_kernel<L, LOOP>, threads, 0);
+  if (per_sm < 1) per_sm = 1;
+  const int wpb = threads / 32;
+  int64_t want = (a.n_units + wpb - 1) / wpb;
+  int64_t grid = (int64_t)sm_count() * per_sm;
+  if (grid > want) grid = want;
+  evaldiff_kernel<L, LOOP><<<(unsigned)grid, threads, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff: launch");
+  return HT_OK;
 }
 
 template <int L>
@@ -66,16 +81,9 @@ int launch_evaldiff_l(const ht_system* s, int64_t n_pts, const double* x, double
   a.val = val;
   a.jac = jac;
   a.n_units = ((n_pts + 31) / 32) * s->np;
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaldiff_kernel<L>, 128, 0);
-  if (per_sm < 1) per_sm = 1;
-  int64_t want = (a.n_units + 3) / 4;  // 4 warps per block
-  int64_t grid = (int64_t)sm_count() * per_sm;
-  if (grid > want) grid = want;
-  evaldiff_kernel<L><<<(unsigned)grid, 128, 0, st>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff: launch");
-  return HT_OK;
+  const int threads = s->eval_threads > 0 ? s->eval_threads : 128;
+  const bool loop = s->eval_variant != 0;  // default: compact bodies
+  return loop ? launch_v<L, true>(a, threads, st) : launch_v<L, false>(a, threads, st);
 }
 
 #ifndef HT_LIMBS

@@ -13,6 +13,8 @@ struct ht_system {
   int nv = 0, np = 0, limbs = 0, device = 0;
   int64_t M = 0, n_pairs = 0;
   int max_k = 0, max_exp = 0, max_deg = 0;
+  int eval_variant = -1;         // 0 unrolled bodies, 1 compact bodies, -1 default (compact)
+  int eval_threads = 0;          // CTA size of the evaluation kernel, 0 = default (128)
   std::vector<int32_t> n_terms;  // host copies
   std::vector<int8_t> exps;
   std::vector<double> coef;
@@ -49,14 +51,7 @@ int sm_count();
 
 template <int L>
 int launch_evaldiff_l(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st);
-inline int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac,
-                           cudaStream_t st) {
-  switch (s->limbs) {
-    case 1: return launch_evaldiff_l<1>(s, n_pts, x, val, jac, st);
-    case 2: return launch_evaldiff_l<2>(s, n_pts, x, val, jac, st);
-    case 4: return launch_evaldiff_l<4>(s, n_pts, x, val, jac, st);
-  }
-  return set_error(HT_EINVAL, "ht_eval_diff: limbs=%d", s->limbs);
-}
+int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac,
+                    cudaStream_t st);
 
 }  // namespace ht

@@ -13,7 +13,10 @@
 //     terms are summed plainly, and the four resulting components are
 //     renormalised by one bottom-up and one top-down sweep of two_sum;
 //   * the complex product computes each component as one fused two-term dot
-//     product (a.re b.re - a.im b.im) instead of two products and a sum.
+//     product (a.re b.re - a.im b.im) instead of two products and a sum;
+//   * the complex quad double operations are out-of-line functions: inlined,
+//     each is a thousand instructions, and the kernels would spend their time
+//     waiting for instruction fetch.
 // The error of every operation is a small multiple of u^L times the sum of the
 // moduli of its operands' terms, which is the scale the library's accuracy
 // contract is stated in.  All primitives use explicitly rounded intrinsics so
@@ -314,17 +317,17 @@ __device__ __forceinline__ cx<2> cscale(cx<2> a, double s) { return cx<2>{dd_mul
 __device__ __forceinline__ cx<2> caxpy(cx<2> acc, double e, cx<2> d) { return cadd(acc, cscale(d, e)); }
 
 // complex quad double
-__device__ __forceinline__ cx<4> cadd(cx<4> a, cx<4> b) { return cx<4>{qd_add(a.re, b.re), qd_add(a.im, b.im)}; }
-__device__ __forceinline__ cx<4> csub(cx<4> a, cx<4> b) { return cx<4>{qd_sub(a.re, b.re), qd_sub(a.im, b.im)}; }
-__device__ __forceinline__ cx<4> cmul(cx<4> a, cx<4> b) {
+static __device__ __noinline__ cx<4> cadd(cx<4> a, cx<4> b) { return cx<4>{qd_add(a.re, b.re), qd_add(a.im, b.im)}; }
+static __device__ __noinline__ cx<4> csub(cx<4> a, cx<4> b) { return cx<4>{qd_sub(a.re, b.re), qd_sub(a.im, b.im)}; }
+static __device__ __noinline__ cx<4> cmul(cx<4> a, cx<4> b) {
   qd x1[2] = {a.re, a.im}, y1[2] = {b.re, b.im};
   const double s1[2] = {1.0, -1.0};
   qd x2[2] = {a.re, a.im}, y2[2] = {b.im, b.re};
   const double s2[2] = {1.0, 1.0};
   return cx<4>{qd_dot<2>(x1, y1, s1), qd_dot<2>(x2, y2, s2)};
 }
-__device__ __forceinline__ cx<4> cscale(cx<4> a, double s) { return cx<4>{qd_mul_d(a.re, s), qd_mul_d(a.im, s)}; }
-__device__ __forceinline__ cx<4> caxpy(cx<4> acc, double e, cx<4> d) { return cadd(acc, cscale(d, e)); }
+static __device__ __noinline__ cx<4> cscale(cx<4> a, double s) { return cx<4>{qd_mul_d(a.re, s), qd_mul_d(a.im, s)}; }
+static __device__ __noinline__ cx<4> caxpy(cx<4> acc, double e, cx<4> d) { return cadd(acc, cscale(d, e)); }
 
 // ------------------------------------------------------------ L-limb reals
 template <int L>
@@ -357,8 +360,8 @@ __device__ __forceinline__ dd r_sqrt(dd a) { return dd_sqrt(a); }
 __device__ __forceinline__ qd r_add(qd a, qd b) { return qd_add(a, b); }
 __device__ __forceinline__ qd r_sub(qd a, qd b) { return qd_sub(a, b); }
 __device__ __forceinline__ qd r_mul(qd a, qd b) { return qd_mul(a, b); }
-__device__ __forceinline__ qd r_div(qd a, qd b) { return qd_div(a, b); }
-__device__ __forceinline__ qd r_sqrt(qd a) { return qd_sqrt(a); }
+static __device__ __noinline__ qd r_div(qd a, qd b) { return qd_div(a, b); }
+static __device__ __noinline__ qd r_sqrt(qd a) { return qd_sqrt(a); }
 template <int L>
 __device__ __forceinline__ rl<L> r_from(double d);
 template <>
@@ -392,7 +395,7 @@ __device__ __forceinline__ bool r_finite(qd a) {
 // |a|^2, conj(a) * b and a * s (s an L-limb real), one rounding per component.
 __device__ __forceinline__ double cabs2(cx<1> a) { return __fma_rn(a.re, a.re, __dmul_rn(a.im, a.im)); }
 __device__ __forceinline__ dd cabs2(cx<2> a) { return dd_dot2(a.re, a.re, a.im, a.im); }
-__device__ __forceinline__ qd cabs2(cx<4> a) {
+static __device__ __noinline__ qd cabs2(cx<4> a) {
   qd x[2] = {a.re, a.im};
   const double s[2] = {1.0, 1.0};
   return qd_dot<2>(x, x, s);
@@ -403,7 +406,7 @@ __device__ __forceinline__ cx<1> cconjmul(cx<1> a, cx<1> b) {
 __device__ __forceinline__ cx<2> cconjmul(cx<2> a, cx<2> b) {
   return cx<2>{dd_dot2(a.re, b.re, a.im, b.im), dd_dot2(a.re, b.im, dd_neg(a.im), b.re)};
 }
-__device__ __forceinline__ cx<4> cconjmul(cx<4> a, cx<4> b) {
+static __device__ __noinline__ cx<4> cconjmul(cx<4> a, cx<4> b) {
   qd x1[2] = {a.re, a.im}, y1[2] = {b.re, b.im};
   const double s1[2] = {1.0, 1.0};
   qd x2[2] = {a.re, a.im}, y2[2] = {b.im, b.re};
@@ -412,7 +415,7 @@ __device__ __forceinline__ cx<4> cconjmul(cx<4> a, cx<4> b) {
 }
 __device__ __forceinline__ cx<1> cscale_r(cx<1> a, double s) { return cscale(a, s); }
 __device__ __forceinline__ cx<2> cscale_r(cx<2> a, dd s) { return cx<2>{dd_mul(a.re, s), dd_mul(a.im, s)}; }
-__device__ __forceinline__ cx<4> cscale_r(cx<4> a, qd s) { return cx<4>{qd_mul(a.re, s), qd_mul(a.im, s)}; }
+static __device__ __noinline__ cx<4> cscale_r(cx<4> a, qd s) { return cx<4>{qd_mul(a.re, s), qd_mul(a.im, s)}; }
 // Modulus from the leading limbs in double (used for norms and tests only).
 template <int L>
 __device__ __forceinline__ double cabs_lead(cx<L> a) {

@@ -31,6 +31,8 @@ SIGNATURES = {
     "ht_system_info": ([P, P, P, P, P], I32),
     "ht_eval_diff": ([P, I64, P, P, P, P], I32),
     "ht_eval_diff_host": ([P, I64, P, P, P, P], I32),
+    "ht_set_eval_config": ([P, I32, I32], I32),
+    "ht_tune_eval": ([P, I64, P, P, P, I32, P, P, P, P], I32),
     "ht_default_params": ([I32, P], I32),
     "ht_start_solutions": ([I32, P, I32, I64, I64, P, P], I32),
     "ht_mgs_solve": ([I32, I32, I32, I64, P, P, P, P], I32),
@@ -164,6 +166,18 @@ def ht_eval_diff(sys: System, n_pts: int, x, val, jac, stream=None) -> None:
 def ht_eval_diff_host(sys: System, n_pts: int, x, val, jac, stream=None) -> None:
     """As ht_eval_diff on host buffers; returns when the results are in host memory."""
     _check(lib().ht_eval_diff_host(sys.handle, n_pts, _ptr(x), _ptr(val), _ptr(jac), _stream(stream)))
+
+
+def ht_set_eval_config(sys: System, variant: int, threads: int) -> None:
+    _check(lib().ht_set_eval_config(sys.handle, variant, threads))
+
+
+def ht_tune_eval(sys: System, n_pts, x, val, jac, reps=3, stream=None):
+    """Returns (variant, threads, best_ms) and keeps that choice in the system."""
+    v, t, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(lib().ht_tune_eval(sys.handle, n_pts, _ptr(x), _ptr(val), _ptr(jac), reps, ctypes.byref(v),
+                              ctypes.byref(t), ctypes.byref(ms), _stream(stream)))
+    return v.value, t.value, ms.value
 
 
 def system_from(system, limbs: int) -> System:

@@ -119,3 +119,32 @@ def test_host_buffer_entry_point_matches(ht, L):
     v1, j1 = _run(ht, s, x, L)
     v2, j2 = _run(ht, s, x, L, host=True)
     assert np.array_equal(v1, v2) and np.array_equal(j1, j2)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_every_kernel_configuration_gives_identical_results(ht, L):
+    """Compact and unrolled monomial bodies, 64/128/256 threads: the same
+    operations in the same order, so bitwise identical outputs; the autotuner
+    then keeps one of them."""
+    s = synth.config_system("c1_evaldiff")
+    n = 32 * 5 + 7
+    x = synth.unit_points(3 + L, s.n_vars, n, L)
+    hs = ht.system_from(s, L)
+    xd = torch.from_numpy(x).cuda()
+    ref = None
+    for variant in (1, 0):
+        for threads in (64, 128, 256):
+            ht.ht_set_eval_config(hs, variant, threads)
+            val = torch.full((s.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+            jac = torch.full((s.n_polys, s.n_vars, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+            ht.ht_eval_diff(hs, n, xd, val, jac)
+            out = (val.cpu().numpy(), jac.cpu().numpy())
+            if ref is None:
+                ref = out
+            else:
+                assert np.array_equal(out[0], ref[0]) and np.array_equal(out[1], ref[1]), (variant, threads)
+    val = torch.empty((s.n_polys, 2, L, n), dtype=torch.float64, device="cuda")
+    jac = torch.empty((s.n_polys, s.n_vars, 2, L, n), dtype=torch.float64, device="cuda")
+    v, t, ms = ht.ht_tune_eval(hs, n, xd, val, jac, reps=1)
+    assert v in (0, 1) and t in (64, 128, 256) and ms > 0
+    assert np.array_equal(val.cpu().numpy(), ref[0])
