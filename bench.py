@@ -75,6 +75,8 @@ def _args():
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--track", default="c0_plain_d,c2_batched_dd",
                    help="tracking workloads to time as well (comma list, '' for none)")
+    p.add_argument("--learned", type=int, default=65536,
+                   help="paths of the held-out n = 16 system for learned vs plain (0: skip)")
     return p.parse_args()
 
 
@@ -193,6 +195,64 @@ def track_workload(ht, torch, name, rank, world, reps=2):
             "converged": d["converged"], "failed": d["failed"], "diverged": d["diverged"],
             "steps_per_path": d["steps"] / m, "newton_per_path": d["newton"] / m, "launches": d["launches"],
             "syncs": d["syncs"]}
+
+
+def _agreement(A, B, tol=1e-10):
+    """Fraction of the endpoints of each set that have a partner in the other
+    within tol * max(1, |x|_inf) (both directions; the smaller fraction)."""
+    from scipy.spatial import cKDTree
+    if len(A) == 0 or len(B) == 0:
+        return 1.0 if len(A) == len(B) else 0.0
+    def emb(X):
+        return np.concatenate([X.real, X.imag], axis=1)
+    fr = []
+    for P, Q in ((A, B), (B, A)):
+        d, _ = cKDTree(emb(Q)).query(emb(P), k=1, p=np.inf)
+        scale = np.maximum(1.0, np.max(np.abs(P), axis=1))
+        fr.append(float(np.mean(d <= tol * scale)))
+    return min(fr)
+
+
+def learned_vs_plain(ht, torch, world, m, n_train=6, train_paths=256, eval_seed=3500):
+    """The learned step against the plain rule on a held-out n = 16 system:
+    the network is trained first (outside the timing) on step-start records
+    of seeded training systems, then both trackers run all m paths."""
+    from paper_1505_00383_gb300 import learned
+    cfg = synth.CONFIGS["c3_learned_d"]
+    prm = ht.ht_default_params(1, h_min=1e-6)
+    t0 = time.perf_counter()
+    feats, labs = [], []
+    for seed in range(cfg["train_seeds"][0], cfg["train_seeds"][0] + n_train):
+        s = synth.config_system("c3_learned_d", seed)
+        g = synth.random_gamma(seed)
+        rec = learned.collect_records(s, 1, g, train_paths, prm, stride=2)
+        labs.append(learned.step_labels(s, 1, g, prm, rec))
+        feats.append(learned.features(s, 1, prm, rec))
+    net, losses = learned.train(torch.cat(feats), torch.cat(labs), epochs=30, batch=2048, lr=2e-3)
+    train_s = time.perf_counter() - t0
+    s = synth.config_system("c3_learned_d", eval_seed)
+    g = synth.random_gamma(eval_seed)
+    out = {}
+    for name, nn in (("plain", None), ("learned", net)):
+        learned.track(s, 1, g, m, prm, net=nn)  # warm-up: workspace, graphs
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        r = learned.track(s, 1, g, m, prm, net=nn)
+        sec = time.perf_counter() - t1
+        out[name] = (r, sec)
+    (ra, sa), (rb, sb) = out["plain"], out["learned"]
+    from_c = lambda r: ((r["x_end"][:, 0, 0, :] + 1j * r["x_end"][:, 1, 0, :]).T)[r["status"] == 1]
+    agree = _agreement(from_c(ra), from_c(rb))
+    counts = lambda r: {k: r["stats"][k] for k in ("converged", "failed", "diverged")}
+    return {"paths": m, "precision": "D", "n": 16, "heldout_seed": eval_seed,
+            "plain_s": sa, "learned_s": sb, "plain_paths_per_s": world * m / sa,
+            "learned_paths_per_s": world * m / sb, "speedup": sa / sb,
+            "newton_per_path": {"plain": ra["stats"]["newton"] / m, "learned": rb["stats"]["newton"] / m},
+            "rejects_per_path": {"plain": ra["stats"]["rejects"] / m, "learned": rb["stats"]["rejects"] / m},
+            "counts": {"plain": counts(ra), "learned": counts(rb)},
+            "counts_equal": counts(ra) == counts(rb), "endpoint_agreement_1e-10": agree,
+            "train": {"systems": n_train, "paths_each": train_paths, "samples": int(sum(f.shape[0] for f in feats)),
+                      "first_loss": float(losses[0]), "last_loss": float(losses[-1]), "seconds": train_s}}
 
 
 def run_reference(a):
@@ -327,6 +387,8 @@ def run_ours(a):
     tracking = {}
     for name in [w for w in a.track.split(",") if w]:
         tracking[name] = track_workload(ht, torch, name, rank, world)
+    if a.learned > 0:
+        tracking["c3_learned_vs_plain"] = learned_vs_plain(ht, torch, world, a.learned)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

@@ -128,6 +128,45 @@ int ht_set_eval_config(ht_system* sys, int variant, int threads);
 int ht_tune_eval(ht_system* sys, int64_t n_pts, const double* x, double* val, double* jac, int reps, int* variant,
                  int* threads, float* best_ms, void* stream);
 
+/* ------------------------------------------------------- learned step MLP */
+
+/*
+ * The learned step-size proposer (a workload addition on top of Section 2,
+ * where the step-size rule is left open): a dense network
+ * 16 -> 64 -> 64 -> 2 with ReLU after both hidden layers.  Inputs are the
+ * per-path step features (ht_track_paths_ex documents them); outputs are
+ * (rho, alpha): the log of the proposed step multiplier and a scale for the
+ * predictor's displacement.  Products run on the tensor cores with BF16
+ * operands and FP32 accumulation; parameters are FP32 masters.
+ * Parameter vector (HT_MLP_NPARAM floats): W1[64][16] b1[64] W2[64][64] b2[64]
+ * W3[2][64] b3[2], weights row-major [out][in].
+ */
+#define HT_MLP_IN 16
+#define HT_MLP_OUT 2
+#define HT_MLP_NPARAM 5378
+typedef struct ht_mlp ht_mlp;
+
+/* Create a network with all parameters zero (set them with ht_mlp_set_params). */
+int ht_mlp_create(ht_mlp** out);
+int ht_mlp_destroy(ht_mlp* net);
+/* Copy parameters from / to host [HT_MLP_NPARAM] floats.  Setting them also
+ * resets the optimiser state. */
+int ht_mlp_set_params(ht_mlp* net, const float* params);
+int ht_mlp_get_params(const ht_mlp* net, float* params);
+/* y = network(x) for B samples: x device [B][16], y device [B][2].  Async. */
+int ht_mlp_forward(const ht_mlp* net, int64_t B, const float* x, float* y, void* stream);
+/* Mean squared error (1/B) sum_b sum_o (y_bo - target_bo)^2 over B samples and
+ * its gradient with respect to the parameters: x device [B][16], target device
+ * [B][2], grad device [HT_MLP_NPARAM] or NULL, loss device [1] or NULL.  Async. */
+int ht_mlp_loss_grad(ht_mlp* net, int64_t B, const float* x, const float* target, float* grad, float* loss,
+                     void* stream);
+/* Train on n samples (x, target as above, device) for `epochs` passes over
+ * consecutive minibatches of `batch` samples (shuffle the data beforehand),
+ * one Adam step (beta 0.9 / 0.999, eps 1e-8) per minibatch at rate lr.
+ * epoch_loss: host [epochs] mean minibatch loss per epoch, or NULL.  Blocks. */
+int ht_mlp_train(ht_mlp* net, int64_t n, const float* x, const float* target, int epochs, int64_t batch, float lr,
+                 float* epoch_loss, void* stream);
+
 /* ---------------------------------------------------------------- tracking */
 
 /* Parameters of the predictor-corrector loop (Section 2 leaves every value
@@ -227,6 +266,77 @@ int ht_compact(const int8_t* status, int64_t m, int32_t* path_idx, int32_t* coun
 int ht_track_paths(ht_system* f, const int32_t* start_deg, const double* gamma, int64_t n_paths, int64_t first_path,
                    const double* x0, const ht_params* p, double* x_end, int8_t* status, double* t_end,
                    int32_t* steps, ht_stats* stats, void* stream);
+
+/*
+ * ht_track_paths_ex -- ht_track_paths with optional extras (io may be NULL,
+ * which makes it ht_track_paths):
+ *
+ *   Restart from recorded states.  init_records (device [n_paths][R] doubles,
+ *   R = ht_record_size(n, L, max_order)) gives every path its t, step size h,
+ *   history of accepted points and last-step summary; x0 and first_path are
+ *   then ignored.  Used to probe what step a state allows (labels for the
+ *   learned step).
+ *
+ *   Step-start recording.  With trace != NULL, the state of each path at the
+ *   start of every trace_stride-th step is written as one record to trace
+ *   (device [trace_capacity][R]); *trace_count (device, zero it first) counts
+ *   the records offered, and those beyond trace_capacity are dropped.
+ *
+ *   Learned step sizes.  With mlp != NULL, at the start of each step the
+ *   network maps the step features (ht_step_features) to rho; the step tried
+ *   is clamp(h exp(clamp(rho, rho_min, rho_max)), h_min, h_max) in place of
+ *   the plain rule's h.  The corrector still judges the step: a rejected
+ *   learned step shrinks as usual and the next fallback_steps steps of that
+ *   path use the plain rule.
+ *
+ * Record layout: 16 header doubles [path index in this call, t, h, number of
+ * history points nh, |dx|_inf and |h|_inf of the last Newton round, rounds of
+ * the last step, last step rejected (0/1), 8 zeros], then the t of the
+ * max_order + 1 history slots, then the history points
+ * [max_order + 1][n][2][L] (oldest first; slots past nh are zero).
+ */
+typedef struct ht_track_io {
+  const double* init_records;
+  double* trace;
+  int64_t trace_capacity;
+  unsigned long long* trace_count;
+  int32_t trace_stride;
+  int32_t fallback_steps;
+  const ht_mlp* mlp;
+  double rho_min, rho_max;
+} ht_track_io;
+
+int ht_track_paths_ex(ht_system* f, const int32_t* start_deg, const double* gamma, int64_t n_paths,
+                      int64_t first_path, const double* x0, const ht_params* p, double* x_end, int8_t* status,
+                      double* t_end, int32_t* steps, ht_stats* stats, const ht_track_io* io, void* stream);
+
+/*
+ * ht_step_labels -- training labels for the learned step: every record is
+ * restarted once per multiplier mu_j (mults host [n_mult], n_mult <= 64) with
+ * its step h scaled by mu_j, and takes one step of at most newton_max
+ * evaluate-correct rounds (p's other settings apply; h_min is lifted).  The
+ * label is rho = log of the largest mu_j whose step was accepted (log of the
+ * smallest mu_j if none was), and 0 for the second output.
+ *   records device [n_rec][R]; labels device [n_rec][2] floats.  Blocks.
+ */
+int ht_step_labels(ht_system* f, const int32_t* start_deg, const double* gamma, const ht_params* p, int64_t n_rec,
+                   const double* records, int n_mult, const double* mults, int newton_max, float* labels,
+                   void* stream);
+
+/* Doubles per step-start record for n variables, `limbs` limbs and predictor
+ * order max_order (-1 for invalid arguments). */
+int64_t ht_record_size(int n, int limbs, int max_order);
+
+/*
+ * ht_step_features -- the 16 inputs of the learned step for each record
+ * (device [n_rec][R] -> device [n_rec][16] floats), computed by the same device
+ * code the tracker uses: t, log10 h, log10 |dx/dt|_inf / 4 (from the last two
+ * accepted points), log10 of the last round's |dx|_inf and |h|_inf / 16, last
+ * step's rounds / newton_max, last step rejected, nh / (max_order + 1),
+ * log10(1 - t) / 16, each clamped to [-4, 4], then zeros.  Async.
+ */
+int ht_step_features(int n, int limbs, int max_order, int newton_max, int64_t n_rec, const double* records,
+                     float* features, void* stream);
 
 /*
  * ht_compact_noalloc -- ht_compact for callers that cannot allocate device

@@ -32,6 +32,7 @@ UNITS = [
     ("ht_track.cu", ["-DHT_LIMBS=4"], "ht_track_4.o"),
     ("ht_track_host.cu", [], "ht_track_host.o"),
     ("ht_noalloc.cu", [], "ht_noalloc.o"),
+    ("ht_mlp.cu", [], "ht_mlp.o"),
 ]
 
 

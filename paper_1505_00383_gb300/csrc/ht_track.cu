@@ -23,6 +23,7 @@
 // paths" of Table tabmemory.
 #include "ht_eval.cuh"
 #include "ht_internal.h"
+#include "ht_mlp.cuh"
 #include "ht_track.h"
 
 namespace ht {
@@ -81,18 +82,96 @@ __global__ void start_kernel(int n, const int32_t* __restrict__ deg, int64_t fir
   }
 }
 
+// Features of a path at the start of a step, for the learned step-size
+// proposer.  History values are read as hv(q) = hx[q * stride] with plane q
+// of the history array ([cap][n][2][L]); t values as tv[j * tstride].
+//   f0 t, f1 log10 h, f2 log10 |dx/dt|_inf / 4 (from the last two accepted
+//   points, 0 with fewer), f3 log10 |dx| of the last round / 16, f4 log10 |h|
+//   of the last round / 16, f5 rounds of the last step / newton_max, f6 last
+//   step rejected, f7 history length / cap, f8 log10(1 - t) / 16; each clamped
+//   to [-4, 4]; f9..f15 zero.
+template <int L>
+__device__ __forceinline__ void step_features(float* f, double t, double h, int nh, int cap, int n,
+                                              const double* tv, int64_t tstride, const double* hx, int64_t stride,
+                                              double last_dx, double last_res, int last_its, int last_rej,
+                                              int newton_max) {
+  double dxdt = 0.0;
+  if (nh >= 2) {
+    const double dt = tv[(int64_t)(nh - 1) * tstride] - tv[(int64_t)(nh - 2) * tstride];
+    double mx = 0.0;
+    for (int i = 0; i < n; ++i) {
+      const int64_t q1 = (((int64_t)(nh - 1) * n + i) * 2) * L, q0 = (((int64_t)(nh - 2) * n + i) * 2) * L;
+      const double dr = hx[q1 * stride] - hx[q0 * stride];
+      const double di = hx[(q1 + L) * stride] - hx[(q0 + L) * stride];
+      mx = fmax(mx, sqrt(dr * dr + di * di));
+    }
+    dxdt = dt > 0.0 ? mx / dt : 0.0;
+  }
+  double v[9] = {t,
+                 log10(h),
+                 log10(dxdt + 1e-30) / 4.0,
+                 log10(last_dx + 1e-300) / 16.0,
+                 log10(last_res + 1e-300) / 16.0,
+                 (double)last_its / (double)newton_max,
+                 (double)last_rej,
+                 (double)nh / (double)cap,
+                 log10(1.0 - t + 1e-16) / 16.0};
+  for (int i = 0; i < 9; ++i) f[i] = (float)fmin(4.0, fmax(-4.0, v[i]));
+  for (int i = 9; i < FEAT; ++i) f[i] = 0.0f;
+}
+
+template <int L>
+__global__ void features_kernel(const double* __restrict__ rec, int64_t n_rec, int n, int cap, int newton_max,
+                                float* __restrict__ feat) {
+  const int64_t R = rec_size(n, L, cap);
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rec; r += (int64_t)gridDim.x * blockDim.x) {
+    const double* h = rec + r * R;
+    step_features<L>(feat + r * FEAT, h[1], h[2], (int)h[3], cap, n, h + REC_HDR, 1, h + REC_HDR + cap, 1, h[4], h[5],
+                     (int)h[6], (int)h[7], newton_max);
+  }
+}
+
 template <int L>
 __global__ void init_kernel(TrackArgs a) {
+  const int cap = a.prm.max_order + 1;
+  const int64_t R = rec_size(a.n, L, cap);
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.m; p += (int64_t)gridDim.x * blockDim.x) {
-    for (int i = 0; i < a.n; ++i) st<L>(a.hx, i, a.m, p, ld<L>(a.x, i, a.m, p));
-    a.ht[p] = 0.0;
-    a.t[p] = 0.0;
-    a.h[p] = a.prm.h0;
+    if (a.init_rec) {  // resume from a recorded step start
+      const double* r = a.init_rec + p * R;
+      int nh = (int)r[3];
+      nh = nh < 1 ? 1 : (nh > cap ? cap : nh);
+      for (int s = 0; s < nh; ++s) {
+        a.ht[(int64_t)s * a.m + p] = r[REC_HDR + s];
+        for (int i = 0; i < a.n; ++i)
+          for (int c = 0; c < 2 * L; ++c)
+            a.hx[(((int64_t)s * a.n + i) * 2 * L + c) * a.m + p] = r[REC_HDR + cap + ((int64_t)s * a.n + i) * 2 * L + c];
+      }
+      for (int i = 0; i < a.n; ++i)
+        for (int c = 0; c < 2 * L; ++c)
+          a.x[((int64_t)i * 2 * L + c) * a.m + p] = r[REC_HDR + cap + ((int64_t)(nh - 1) * a.n + i) * 2 * L + c];
+      a.t[p] = r[1];
+      a.h[p] = r[2];
+      a.nh[p] = (int8_t)nh;
+      a.last_dx[p] = r[4];
+      a.last_res[p] = r[5];
+      a.last_its[p] = (int8_t)r[6];
+      a.last_rej[p] = (int8_t)r[7];
+    } else {
+      for (int i = 0; i < a.n; ++i) st<L>(a.hx, i, a.m, p, ld<L>(a.x, i, a.m, p));
+      a.ht[p] = 0.0;
+      a.t[p] = 0.0;
+      a.h[p] = a.prm.h0;
+      a.nh[p] = 1;
+      a.last_dx[p] = 0.0;
+      a.last_res[p] = 0.0;
+      a.last_its[p] = 0;
+      a.last_rej[p] = 0;
+    }
     a.t1[p] = 0.0;
     a.status[p] = 0;
     a.it[p] = 0;
     a.phase[p] = PH_TRACK;
-    a.nh[p] = 1;
+    a.fallback[p] = 0;
     a.steps[p] = 0;
     a.rejects[p] = 0;
     a.newton[p] = 0;
@@ -167,9 +246,19 @@ __global__ void __launch_bounds__(32) mgs_kernel(double* A, double* R, double* x
 }
 
 // One Newton step (plus the bookkeeping around it) for `iters` rounds.
-template <int L>
+// LEARN: at every step start warp 0 evaluates the step-size network for its 32
+// paths on the tensor cores and scales the step (see ht_track_paths_ex).
+template <int L, bool LEARN>
 __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
   __shared__ double red[4][8][32];  // per-warp partials: residual, update, point norms; finiteness
+  __shared__ double sh_h[32];       // learned step of each lane's path
+  __shared__ long long sh_slot[32]; // trace record slot of each lane's path (-1: none)
+  extern __shared__ __align__(16) unsigned char dsm[];  // network image when LEARN
+  if constexpr (LEARN) {
+    mlp_load(*reinterpret_cast<MlpSmem*>(dsm), a.mlp_wbf, a.mlp_master);
+    __syncthreads();
+  }
+  const int cap = a.prm.max_order + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, T = blockDim.x >> 5;
   const int n = a.n, W = n + 1;
   const int64_t m = a.m;
@@ -197,8 +286,68 @@ __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
       int it = act ? a.it[p] : 0;
       double t = act ? a.t[p] : 0.0, h = act ? a.h[p] : 0.0, t1 = act ? a.t1[p] : 0.0;
       int nh = act ? a.nh[p] : 1;
+      int fb = act ? a.fallback[p] : 0;
+      const bool start = act && ph == PH_TRACK && it == 0;
+      // ---- A0: record the step start, propose a learned step
+      if (a.trace) {
+        if (warp == 0) {
+          long long slot = -1;
+          if (start && a.steps[p] % a.trace_stride == 0) {
+            slot = (long long)atomicAdd(a.trace_count, 1ULL);
+            if (slot >= a.trace_cap) slot = -1;
+          }
+          sh_slot[lane] = slot;
+          if (slot >= 0) {
+            double* r = a.trace + slot * rec_size(n, L, cap);
+            r[0] = (double)p;
+            r[1] = t;
+            r[2] = h;
+            r[3] = (double)nh;
+            r[4] = a.last_dx[p];
+            r[5] = a.last_res[p];
+            r[6] = (double)a.last_its[p];
+            r[7] = (double)a.last_rej[p];
+            for (int k = 8; k < REC_HDR; ++k) r[k] = 0.0;
+            for (int s2 = 0; s2 < cap; ++s2) r[REC_HDR + s2] = s2 < nh ? a.ht[(int64_t)s2 * m + p] : 0.0;
+          }
+        }
+        __syncthreads();
+        const long long slot = sh_slot[lane];
+        if (slot >= 0) {
+          double* r = a.trace + slot * rec_size(n, L, cap) + REC_HDR + cap;
+          for (int s2 = 0; s2 < cap; ++s2)
+            for (int i = warp; i < n; i += T)
+              for (int c = 0; c < 2 * L; ++c)
+                r[((int64_t)s2 * n + i) * 2 * L + c] =
+                    s2 < nh ? a.hx[(((int64_t)s2 * n + i) * 2 * L + c) * m + p] : 0.0;
+        }
+      }
+      if constexpr (LEARN) {
+        if (warp == 0) {
+          float f[FEAT];
+          if (start && fb == 0)
+            step_features<L>(f, t, h, nh, cap, n, a.ht + p, m, a.hx + p, m, a.last_dx[p], a.last_res[p],
+                             (int)a.last_its[p], (int)a.last_rej[p], a.prm.newton_max);
+          else
+            for (int i = 0; i < FEAT; ++i) f[i] = 0.0f;
+          float y[2];
+          mlp_forward_warp(*reinterpret_cast<const MlpSmem*>(dsm),
+                           *reinterpret_cast<MlpWarpSmem*>(dsm + sizeof(MlpSmem)), f, y);
+          double hs = h;
+          if (start && fb == 0) {
+            const double rho = fmin(a.rho_max, fmax(a.rho_min, (double)y[0]));
+            hs = fmin(a.prm.h_max, fmax(a.prm.h_min, h * exp(rho)));
+          }
+          sh_h[lane] = hs;
+        }
+        __syncthreads();
+        if (start && fb == 0) {
+          h = sh_h[lane];
+          fb = -1;  // this step is a learned one
+        }
+      }
       // ---- A: predictor (first Newton round of a step) or polish copy
-      if (act && ph == PH_TRACK && it == 0) {
+      if (start) {
         double step = fmin(h, 1.0 - t);
         t1 = (step >= 1.0 - t) ? 1.0 : t + step;
         const int mm = min(nh, a.prm.max_order + 1);
@@ -275,6 +424,8 @@ __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
       // ---- E: the state machine of a step (identical in every warp)
       bool accept_point = false;  // copy xp into x (and maybe history)
       bool push_hist = false;
+      bool step_end = false;
+      int last_its_v = 0, last_rej_v = 0;
       int newton = 0, steps = 0, rejects = 0;
       if (act) {
         newton = a.newton[p] + 1;
@@ -292,6 +443,13 @@ __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
           }
           if (ok || nan || it >= a.prm.newton_max) {  // the step ends here
             ++steps;
+            last_its_v = it;
+            last_rej_v = ok ? 0 : 1;
+            step_end = true;
+            if (fb == -1)
+              fb = ok ? 0 : a.fallback_steps;
+            else if (fb > 0)
+              --fb;
             it = 0;
             if (ok) {
               t = t1;
@@ -377,6 +535,13 @@ __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
         a.steps[p] = steps;
         a.rejects[p] = rejects;
         a.newton[p] = newton;
+        a.fallback[p] = (int8_t)fb;
+        if (step_end) {
+          a.last_dx[p] = ndx;
+          a.last_res[p] = nres;
+          a.last_its[p] = (int8_t)last_its_v;
+          a.last_rej[p] = (int8_t)last_rej_v;
+        }
       }
       __syncthreads();
     }
@@ -463,21 +628,41 @@ int launch_init_l(const TrackArgs& a, cudaStream_t st) {
 
 template <int L>
 int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_t st) {
+  const bool learn = a.mlp_wbf != nullptr;
+  const size_t dsm = learn ? sizeof(MlpSmem) + sizeof(MlpWarpSmem) : 0;
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L>, 32 * team, 0);
+  if (learn) {
+    cudaFuncSetAttribute(track_kernel<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L, true>, 32 * team, dsm);
+  } else {
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L, false>, 32 * team, 0);
+  }
   if (per_sm < 1) per_sm = 1;
   int64_t grid = (int64_t)sm_count() * per_sm;
   if (grid > max_groups) grid = max_groups;
   if (grid < 1) grid = 1;
-  track_kernel<L><<<(unsigned)grid, 32 * team, 0, st>>>(a);
+  if (learn)
+    track_kernel<L, true><<<(unsigned)grid, 32 * team, dsm, st>>>(a);
+  else
+    track_kernel<L, false><<<(unsigned)grid, 32 * team, 0, st>>>(a);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HT_OK : cuda_fail(e, "track launch");
 }
 
 template <int L>
+int launch_features_l(const double* rec, int64_t n_rec, int n, int cap, int newton_max, float* feat, cudaStream_t st) {
+  if (n_rec == 0) return HT_OK;
+  int64_t blocks = (n_rec + 127) / 128;
+  if (blocks > 4096) blocks = 4096;
+  features_kernel<L><<<(unsigned)blocks, 128, 0, st>>>(rec, n_rec, n, cap, newton_max, feat);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "features launch");
+}
+
+template <int L>
 int track_occupancy_l(int team) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L>, 32 * team, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L, false>, 32 * team, 0);
   return per_sm;
 }
 
@@ -489,5 +674,6 @@ template int launch_mgs_l<HT_LIMBS>(double*, double*, double*, int, int, int64_t
 template int launch_init_l<HT_LIMBS>(const TrackArgs&, cudaStream_t);
 template int launch_track_l<HT_LIMBS>(const TrackArgs&, int, int64_t, cudaStream_t);
 template int track_occupancy_l<HT_LIMBS>(int);
+template int launch_features_l<HT_LIMBS>(const double*, int64_t, int, int, int, float*, cudaStream_t);
 
 }  // namespace ht

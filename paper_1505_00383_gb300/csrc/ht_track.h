@@ -3,9 +3,21 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <cuda_bf16.h>
+
 #include <cstdint>
 
 namespace ht {
+
+// Step-start record (doubles): a 16-double header
+//   [0] path id  [1] t  [2] h  [3] nh  [4] |dx| of the last round  [5] |h| of
+//   the last round  [6] rounds of the last step  [7] last step rejected
+//   [8..15] zero
+// then t of the cap history points, then the history points [cap][n][2][L]
+// (cap = max_order + 1, oldest first; entries past nh are zero).
+constexpr int REC_HDR = 16;
+inline __host__ __device__ int64_t rec_size(int n, int L, int cap) { return REC_HDR + cap + (int64_t)cap * n * 2 * L; }
+constexpr int FEAT = 16;
 
 struct TrackPrm {
   double h0, h_min, h_max, f_up, f_down, tol_dx, tol_res, tol_polish, r_div;
@@ -46,6 +58,22 @@ struct TrackArgs {
   const int32_t* count_in; // their number (device)
   int32_t* idx0;           // init: identity index list
   int32_t* count0;
+  // last step summary (features of the learned step) and learned-step state
+  double* last_dx;
+  double* last_res;
+  int8_t* last_its;
+  int8_t* last_rej;
+  int8_t* fallback;        // plain steps left after a rejected learned step
+  // optional: start from records, record step starts, learned proposals
+  const double* init_rec;  // [m][rec] or nullptr
+  double* trace;           // [trace_cap][rec] or nullptr
+  unsigned long long* trace_count;
+  int64_t trace_cap;
+  int trace_stride;
+  const __nv_bfloat16* mlp_wbf;  // nullptr: plain rule
+  const float* mlp_master;
+  int fallback_steps;
+  double rho_min, rho_max;
 };
 
 template <int L>
@@ -58,6 +86,8 @@ template <int L>
 int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_t st);
 template <int L>
 int track_occupancy_l(int team);
+template <int L>
+int launch_features_l(const double* rec, int64_t n_rec, int n, int cap, int newton_max, float* feat, cudaStream_t st);
 int launch_compact(const int32_t* idx_in, const int32_t* count_in, const int8_t* status, int32_t* idx_out,
                    int32_t* count_out, cudaStream_t st);
 

@@ -9,6 +9,11 @@
 #include "ht_track.h"
 
 namespace ht {
+const float* mlp_master(const ht_mlp* net);
+const __nv_bfloat16* mlp_bf16(const ht_mlp* net);
+}
+
+namespace ht {
 
 template <typename F>
 static int by_limbs(int L, F f) {
@@ -44,6 +49,36 @@ static int ensure_track_ws(ht_system* s, size_t bytes, cudaStream_t st) {
     if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: pinned count");
   }
   return HT_OK;
+}
+
+// Probe records: record r repeated for every multiplier, its step scaled.
+__global__ void probe_records_kernel(const double* __restrict__ rec, int64_t n_rec, int64_t R, int n_mult,
+                                     const double* __restrict__ mults, double* __restrict__ out) {
+  const int64_t total = n_rec * n_mult * R;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t q = e / R, k = e % R, r = q / n_mult;
+    const int j = (int)(q % n_mult);
+    double v = rec[r * R + k];
+    if (k == 2) v *= mults[j];
+    out[e] = v;
+  }
+}
+
+// Label of record r: rho = log of the largest multiplier whose single probe
+// step was accepted (t moved past the record's t), else log of the smallest.
+__global__ void labels_kernel(const double* __restrict__ rec, int64_t n_rec, int64_t R, int n_mult,
+                              const double* __restrict__ mults, const double* __restrict__ t_end,
+                              float* __restrict__ labels) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rec; r += (int64_t)gridDim.x * blockDim.x) {
+    const double t0 = rec[r * R + 1];
+    double best = -1.0, lo = mults[0];
+    for (int j = 0; j < n_mult; ++j) {
+      lo = fmin(lo, mults[j]);
+      if (t_end[r * n_mult + j] > t0) best = fmax(best, mults[j]);
+    }
+    labels[r * 2 + 0] = (float)log(best > 0.0 ? best : lo);
+    labels[r * 2 + 1] = 0.0f;
+  }
 }
 
 static void drop_graphs(ht_system* s) {
@@ -137,9 +172,9 @@ int ht_compact(const int8_t* status, int64_t m, int32_t* path_idx, int32_t* coun
   return rc;
 }
 
-int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, int64_t n_paths, int64_t first_path,
-                   const double* x0, const ht_params* prm_in, double* x_end, int8_t* status, double* t_end,
-                   int32_t* steps, ht_stats* stats, void* stream) {
+int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamma, int64_t n_paths,
+                      int64_t first_path, const double* x0, const ht_params* prm_in, double* x_end, int8_t* status,
+                      double* t_end, int32_t* steps, ht_stats* stats, const ht_track_io* io, void* stream) {
   clear_error();
   auto t_start = std::chrono::steady_clock::now();
   if (!s) return set_error(HT_EINVAL, "ht_track_paths: NULL system");
@@ -165,6 +200,16 @@ int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, 
       P.max_order < 0 || P.max_order > 7 || P.team_warps < 0 || P.team_warps > 8 || P.iters_per_launch < 0 ||
       P.rounds_per_sync < 0 || (P.rounds_per_sync & 1) || !(P.tol_dx > 0) || !(P.tol_res > 0) || !(P.tol_polish > 0) || !(P.r_div > 0))
     return set_error(HT_EINVAL, "ht_track_paths: invalid parameters");
+  ht_track_io IO;
+  std::memset(&IO, 0, sizeof IO);
+  if (io) IO = *io;
+  if (IO.trace && (IO.trace_stride < 1 || IO.trace_capacity < 0 || !IO.trace_count || !is_device_ptr(IO.trace) ||
+                   !is_device_ptr(IO.trace_count)))
+    return set_error(HT_EINVAL, "ht_track_paths_ex: trace needs a device buffer, a device counter and stride >= 1");
+  if (IO.init_records && !is_device_ptr(IO.init_records))
+    return set_error(HT_EINVAL, "ht_track_paths_ex: init_records must be device memory");
+  if (IO.mlp && (IO.fallback_steps < 0 || IO.fallback_steps > 100 || !(IO.rho_max >= IO.rho_min)))
+    return set_error(HT_EINVAL, "ht_track_paths_ex: invalid learned-step settings");
   if (stats) std::memset(stats, 0, sizeof *stats);
   if (n_paths == 0) return HT_OK;
   if (!x_end || !status || !t_end || !is_device_ptr(x_end) || !is_device_ptr(status) || !is_device_ptr(t_end) ||
@@ -185,7 +230,8 @@ int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, 
          o_A = take((size_t)n * (n + 1) * cxb), o_R = take((size_t)n * (n + 1) * cxb), o_dx = take(n * cxb),
          o_h = take(m * 8), o_t1 = take(m * 8), o_it = take(m), o_ph = take(m), o_nh = take(m),
          o_steps = take(m * 4), o_rej = take(m * 4), o_newt = take(m * 4), o_idx0 = take((m + 1) * 4),
-         o_idx1 = take((m + 1) * 4), o_cnt = take(2 * 4), o_deg = take(n * 4);
+         o_idx1 = take((m + 1) * 4), o_cnt = take(2 * 4), o_deg = take(n * 4), o_ldx = take(m * 8),
+         o_lres = take(m * 8), o_lits = take(m), o_lrej = take(m), o_fb = take(m);
   int rc = ensure_track_ws(s, off, st);
   if (rc != HT_OK) return rc;
   char* w = (char*)s->d_track_ws;
@@ -222,9 +268,26 @@ int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, 
   int32_t* cnt[2] = {(int32_t*)(w + o_cnt), (int32_t*)(w + o_cnt) + 1};
   a.idx0 = idx[0];
   a.count0 = cnt[0];
+  a.last_dx = (double*)(w + o_ldx);
+  a.last_res = (double*)(w + o_lres);
+  a.last_its = (int8_t*)(w + o_lits);
+  a.last_rej = (int8_t*)(w + o_lrej);
+  a.fallback = (int8_t*)(w + o_fb);
+  a.init_rec = IO.init_records;
+  a.trace = IO.trace;
+  a.trace_count = (unsigned long long*)IO.trace_count;
+  a.trace_cap = IO.trace_capacity;
+  a.trace_stride = IO.trace_stride > 0 ? IO.trace_stride : 1;
+  a.mlp_wbf = IO.mlp ? mlp_bf16(IO.mlp) : nullptr;
+  a.mlp_master = IO.mlp ? mlp_master(IO.mlp) : nullptr;
+  a.fallback_steps = IO.fallback_steps;
+  a.rho_min = IO.rho_min;
+  a.rho_max = IO.rho_max;
   cudaError_t e = cudaMemcpyAsync((void*)a.deg, start_deg, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: upload degrees");
-  if (x0) {
+  if (IO.init_records) {
+    // the init kernel takes every path's state from its record
+  } else if (x0) {
     e = cudaMemcpyAsync(x_end, x0, n * cxb, cudaMemcpyDeviceToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: copy x0");
   } else {
@@ -326,6 +389,87 @@ int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, 
     stats->ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
   }
   return HT_OK;
+}
+
+}  // extern "C"
+
+extern "C" {
+
+int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, int64_t n_paths, int64_t first_path,
+                   const double* x0, const ht_params* p, double* x_end, int8_t* status, double* t_end, int32_t* steps,
+                   ht_stats* stats, void* stream) {
+  return ht_track_paths_ex(s, start_deg, gamma, n_paths, first_path, x0, p, x_end, status, t_end, steps, stats,
+                           nullptr, stream);
+}
+
+int ht_step_labels(ht_system* s, const int32_t* start_deg, const double* gamma, const ht_params* prm, int64_t n_rec,
+                   const double* records, int n_mult, const double* mults, int newton_max, float* labels,
+                   void* stream) {
+  clear_error();
+  if (!s || !prm || n_rec < 0 || n_mult < 1 || n_mult > 64 || !mults || newton_max < 1)
+    return set_error(HT_EINVAL, "ht_step_labels: bad arguments");
+  for (int j = 0; j < n_mult; ++j)
+    if (!(mults[j] > 0)) return set_error(HT_EINVAL, "ht_step_labels: multipliers must be positive");
+  if (n_rec == 0) return HT_OK;
+  if (!records || !labels || !is_device_ptr(records) || !is_device_ptr(labels))
+    return set_error(HT_EINVAL, "ht_step_labels: buffers must be device memory");
+  const int n = s->nv, L = s->limbs;
+  const int64_t R = rec_size(n, L, prm->max_order + 1), P = n_rec * n_mult;
+  if (P > 0x7fffffff) return set_error(HT_EINVAL, "ht_step_labels: too many probes");
+  cudaStream_t st = (cudaStream_t)stream;
+  size_t b_rec = (size_t)P * R * 8, b_x = (size_t)n * 2 * L * P * 8, b_t = (size_t)P * 8, b_m = 64 * 8;
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc((void**)&buf, b_rec + b_x + b_t + (size_t)P + b_m + 1024);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(HT_ENOMEM, "ht_step_labels: probe workspace");
+  }
+  double* prec = (double*)buf;
+  double* px = (double*)(buf + b_rec);
+  double* pt = (double*)(buf + b_rec + b_x);
+  double* pm = (double*)(buf + b_rec + b_x + b_t);
+  int8_t* pst = (int8_t*)(buf + b_rec + b_x + b_t + b_m);
+  int rc = HT_OK;
+  e = cudaMemcpyAsync(pm, mults, n_mult * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = cuda_fail(e, "ht_step_labels");
+  if (rc == HT_OK) {
+    probe_records_kernel<<<1024, 256, 0, st>>>(records, n_rec, R, n_mult, pm, prec);
+    ht_params pp = *prm;
+    pp.max_steps = 1;
+    pp.newton_max = newton_max;
+    pp.polish_max = 0;
+    pp.h_min = 1e-300;
+    ht_track_io io;
+    std::memset(&io, 0, sizeof io);
+    io.init_records = prec;
+    rc = ht_track_paths_ex(s, start_deg, gamma, P, 0, nullptr, &pp, px, pst, pt, nullptr, nullptr, &io, stream);
+  }
+  if (rc == HT_OK) {
+    labels_kernel<<<256, 256, 0, st>>>(records, n_rec, R, n_mult, pm, pt, labels);
+    e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ht_step_labels");
+  }
+  cudaFree(buf);
+  return rc;
+}
+
+int64_t ht_record_size(int n, int limbs, int max_order) {
+  if (n < 1 || (limbs != 1 && limbs != 2 && limbs != 4) || max_order < 0 || max_order > 7) return -1;
+  return rec_size(n, limbs, max_order + 1);
+}
+
+int ht_step_features(int n, int limbs, int max_order, int newton_max, int64_t n_rec, const double* records,
+                     float* features, void* stream) {
+  clear_error();
+  if (ht_record_size(n, limbs, max_order) < 0 || newton_max < 1 || n_rec < 0)
+    return set_error(HT_EINVAL, "ht_step_features: bad arguments");
+  if (n_rec == 0) return HT_OK;
+  if (!records || !features || !is_device_ptr(records) || !is_device_ptr(features))
+    return set_error(HT_EINVAL, "ht_step_features: buffers must be device memory");
+  cudaStream_t st = (cudaStream_t)stream;
+  return by_limbs(limbs, [&](auto c) {
+    return launch_features_l<decltype(c)::value>(records, n_rec, n, max_order + 1, newton_max, features, st);
+  });
 }
 
 }  // extern "C"

@@ -33,12 +33,23 @@ SIGNATURES = {
     "ht_eval_diff_host": ([P, I64, P, P, P, P], I32),
     "ht_set_eval_config": ([P, I32, I32], I32),
     "ht_tune_eval": ([P, I64, P, P, P, I32, P, P, P, P], I32),
+    "ht_mlp_create": ([ctypes.POINTER(P)], I32),
+    "ht_mlp_destroy": ([P], I32),
+    "ht_mlp_set_params": ([P, P], I32),
+    "ht_mlp_get_params": ([P, P], I32),
+    "ht_mlp_forward": ([P, I64, P, P, P], I32),
+    "ht_mlp_loss_grad": ([P, I64, P, P, P, P, P], I32),
+    "ht_mlp_train": ([P, I64, P, P, I32, I64, ctypes.c_float, P, P], I32),
     "ht_default_params": ([I32, P], I32),
     "ht_start_solutions": ([I32, P, I32, I64, I64, P, P], I32),
     "ht_mgs_solve": ([I32, I32, I32, I64, P, P, P, P], I32),
     "ht_compact": ([P, I64, P, P, P], I32),
     "ht_compact_noalloc": ([P, I64, P, P, P], I32),
     "ht_track_paths": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P], I32),
+    "ht_track_paths_ex": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P, P], I32),
+    "ht_record_size": ([I32, I32, I32], I64),
+    "ht_step_labels": ([P, P, P, P, I64, P, I32, P, I32, P, P], I32),
+    "ht_step_features": ([I32, I32, I32, I32, I64, P, P, P], I32),
     "ht_bench_fp64_rate": ([I32, ctypes.POINTER(ctypes.c_double), P], I32),
 }
 
@@ -49,6 +60,12 @@ class ht_params(ctypes.Structure):
                                                 "tol_polish", "r_div")] + \
                [(k, ctypes.c_int32) for k in ("newton_max", "polish_max", "max_steps", "max_order", "team_warps",
                                                "iters_per_launch", "rounds_per_sync")]
+
+
+class ht_track_io(ctypes.Structure):
+    _fields_ = [("init_records", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64),
+                ("trace_count", ctypes.c_void_p), ("trace_stride", ctypes.c_int32), ("fallback_steps", ctypes.c_int32),
+                ("mlp", ctypes.c_void_p), ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double)]
 
 
 class ht_stats(ctypes.Structure):
@@ -235,3 +252,94 @@ def ht_track_paths(sys: System, start_deg, gamma, n_paths, first_path, x0, param
     sp = None if stats is None else ctypes.byref(stats)
     _check(lib().ht_track_paths(sys.handle, _ptr(d), _ptr(g), n_paths, first_path, _ptr(x0), pp, _ptr(x_end),
                                 _ptr(status), _ptr(t_end), _ptr(steps), sp, _stream(stream)))
+
+
+HT_MLP_IN, HT_MLP_OUT, HT_MLP_NPARAM = 16, 2, 5378
+
+
+class Mlp:
+    """Owner of an ht_mlp handle."""
+
+    def __init__(self, handle: int):
+        self.handle = handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.ht_mlp_destroy(self.handle)
+            self.handle = None
+
+
+def ht_mlp_create() -> Mlp:
+    out = P()
+    _check(lib().ht_mlp_create(ctypes.byref(out)))
+    return Mlp(out.value)
+
+
+def ht_mlp_destroy(net: Mlp) -> None:
+    if net.handle:
+        _check(lib().ht_mlp_destroy(net.handle))
+        net.handle = None
+
+
+def ht_mlp_set_params(net: Mlp, params) -> None:
+    import numpy as np
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    assert p.size == HT_MLP_NPARAM
+    _check(lib().ht_mlp_set_params(net.handle, _ptr(p)))
+
+
+def ht_mlp_get_params(net: Mlp):
+    import numpy as np
+    p = np.empty(HT_MLP_NPARAM, dtype=np.float32)
+    _check(lib().ht_mlp_get_params(net.handle, _ptr(p)))
+    return p
+
+
+def ht_mlp_forward(net: Mlp, B, x, y, stream=None) -> None:
+    _check(lib().ht_mlp_forward(net.handle, B, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def ht_mlp_loss_grad(net: Mlp, B, x, target, grad, loss, stream=None) -> None:
+    _check(lib().ht_mlp_loss_grad(net.handle, B, _ptr(x), _ptr(target), _ptr(grad), _ptr(loss), _stream(stream)))
+
+
+def ht_mlp_train(net: Mlp, n, x, target, epochs, batch, lr, stream=None):
+    import numpy as np
+    losses = np.zeros(epochs, dtype=np.float32)
+    _check(lib().ht_mlp_train(net.handle, n, _ptr(x), _ptr(target), epochs, batch, ctypes.c_float(lr), _ptr(losses),
+                              _stream(stream)))
+    return losses
+
+
+def ht_record_size(n, limbs, max_order=4) -> int:
+    r = lib().ht_record_size(n, limbs, max_order)
+    if r < 0:
+        raise HTError(HT_EINVAL, "ht_record_size: bad arguments")
+    return r
+
+
+def ht_step_features(n, limbs, max_order, newton_max, n_rec, records, features, stream=None) -> None:
+    _check(lib().ht_step_features(n, limbs, max_order, newton_max, n_rec, _ptr(records), _ptr(features),
+                                  _stream(stream)))
+
+
+def ht_track_paths_ex(sys: System, start_deg, gamma, n_paths, first_path, x0, params, x_end, status, t_end,
+                      steps=None, stats=None, io: "ht_track_io | None" = None, stream=None) -> None:
+    import numpy as np
+    d = np.ascontiguousarray(start_deg, dtype=np.int32)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    pp = None if params is None else ctypes.byref(params)
+    sp = None if stats is None else ctypes.byref(stats)
+    ip = None if io is None else ctypes.byref(io)
+    _check(lib().ht_track_paths_ex(sys.handle, _ptr(d), _ptr(g), n_paths, first_path, _ptr(x0), pp, _ptr(x_end),
+                                   _ptr(status), _ptr(t_end), _ptr(steps), sp, ip, _stream(stream)))
+
+
+def ht_step_labels(sys: System, start_deg, gamma, params, n_rec, records, mults, newton_max, labels,
+                   stream=None) -> None:
+    import numpy as np
+    d = np.ascontiguousarray(start_deg, dtype=np.int32)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    mu = np.ascontiguousarray(mults, dtype=np.float64)
+    _check(lib().ht_step_labels(sys.handle, _ptr(d), _ptr(g), ctypes.byref(params), n_rec, _ptr(records), mu.size,
+                                _ptr(mu), newton_max, _ptr(labels), _stream(stream)))

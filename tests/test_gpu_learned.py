@@ -1,0 +1,194 @@
+"""The learned step: network kernels against the oracle's fp64 network, the
+tracker's record/restart machinery, and what the trained network gains over
+the plain step rule on held-out systems."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from match import match_sets, to_complex
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ht():
+    from paper_1505_00383_gb300 import _build, ht as binding
+    _build.build()
+    oracle.build()
+    assert torch.cuda.is_available()
+    return binding
+
+
+def _bf16(a):
+    return torch.from_numpy(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def _net(ht, params):
+    net = ht.ht_mlp_create()
+    ht.ht_mlp_set_params(net, params)
+    return net
+
+
+def _rand_params(seed, scale=0.3):
+    rng = synth.SplitMix64(seed)
+    return ((rng.uniform(5378) * 2 - 1) * scale).astype(np.float32)
+
+
+@pytest.mark.parametrize("B", [1, 37, 100, 4096 + 17])
+def test_network_forward_matches_oracle(ht, B):
+    """Tensor-core forward (BF16 operands, FP32 accumulation) against the fp64
+    oracle on the same BF16-rounded weights and inputs: BF16 rounding of the
+    hidden activations bounds the difference (~1e-2 relative)."""
+    p = _rand_params(11)
+    rng = synth.SplitMix64(B)
+    x = (rng.uniform(B * 16).reshape(B, 16) * 2 - 1).astype(np.float32)
+    net = _net(ht, p)
+    y = torch.empty((B, 2), dtype=torch.float32, device="cuda")
+    ht.ht_mlp_forward(net, B, torch.from_numpy(x).cuda(), y)
+    torch.cuda.synchronize()
+    pb = p.astype(np.float64).copy()
+    wmask = np.ones(5378, bool)
+    for off, cnt in ((1024, 64), (1024 + 64 + 4096, 64), (5376, 2)):  # biases stay FP32
+        wmask[off:off + cnt] = False
+    pb[wmask] = _bf16(p[wmask])
+    ref = oracle.mlp_forward(_bf16(x), pb)
+    err = np.linalg.norm(y.cpu().numpy() - ref) / max(np.linalg.norm(ref), 1e-30)
+    assert err <= 2e-2, err
+
+
+def test_network_gradient_matches_oracle(ht):
+    B = 333
+    p = _rand_params(12)
+    rng = synth.SplitMix64(5)
+    x = (rng.uniform(B * 16).reshape(B, 16) * 2 - 1).astype(np.float32)
+    tgt = (rng.uniform(B * 2).reshape(B, 2) - 0.5).astype(np.float32)
+    net = _net(ht, p)
+    g = torch.empty((5378,), dtype=torch.float32, device="cuda")
+    loss = torch.empty((1,), dtype=torch.float32, device="cuda")
+    ht.ht_mlp_loss_grad(net, B, torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda(), g, loss)
+    torch.cuda.synchronize()
+    pb = p.astype(np.float64).copy()
+    wmask = np.ones(5378, bool)
+    for off, cnt in ((1024, 64), (1024 + 64 + 4096, 64), (5376, 2)):
+        wmask[off:off + cnt] = False
+    pb[wmask] = _bf16(p[wmask])
+    ref_loss, ref_g = oracle.mlp_loss_grad(_bf16(x), tgt.astype(np.float64), pb)
+    gg = g.cpu().numpy().astype(np.float64)
+    assert abs(loss.item() - ref_loss) <= 2e-2 * ref_loss
+    cos = gg @ ref_g / (np.linalg.norm(gg) * np.linalg.norm(ref_g))
+    assert cos >= 0.999 and np.linalg.norm(gg - ref_g) <= 5e-2 * np.linalg.norm(ref_g), (cos,)
+
+
+def test_training_fits_a_teacher_network(ht):
+    """Adam on the GPU drives the loss of a student well below its start on
+    targets produced by a random teacher network."""
+    n = 16384
+    rng = synth.SplitMix64(21)
+    x = (rng.uniform(n * 16).reshape(n, 16) * 2 - 1).astype(np.float32)
+    teacher = _rand_params(22, 0.25).astype(np.float64)
+    tgt = oracle.mlp_forward(x.astype(np.float64), teacher).astype(np.float32)
+    from paper_1505_00383_gb300 import learned
+    net = _net(ht, learned.init_params(3))
+    losses = ht.ht_mlp_train(net, n, torch.from_numpy(x).cuda(), torch.from_numpy(tgt).cuda(), 40, 1024, 3e-3)
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.1 * losses[0], losses
+
+
+def test_zero_network_tracks_exactly_like_the_plain_rule(ht):
+    """rho = 0 proposes the plain rule's step, so the learned path machinery
+    reproduces the plain tracker bitwise."""
+    from paper_1505_00383_gb300 import learned
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    prm = ht.ht_default_params(1, h_min=1e-6)
+    plain = learned.track(s, 1, gam, 64, prm)
+    net = _net(ht, np.zeros(5378, np.float32))
+    lrn = learned.track(s, 1, gam, 64, prm, net=net)
+    assert np.array_equal(plain["x_end"], lrn["x_end"]) and np.array_equal(plain["status"], lrn["status"])
+    assert plain["stats"]["newton"] == lrn["stats"]["newton"]
+
+
+def test_restart_from_recorded_states_reproduces_the_run(ht):
+    """A path restarted from a recorded step start repeats the same arithmetic
+    and ends where the uninterrupted run ended, bitwise."""
+    from paper_1505_00383_gb300 import learned
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    prm = ht.ht_default_params(1, h_min=1e-6)
+    full = learned.track(s, 1, gam, 64, prm)
+    rec = learned.collect_records(s, 1, gam, 64, prm, stride=5)
+    assert rec.shape[0] > 64
+    # the last record of each path
+    pid = rec[:, 0].cpu().numpy().astype(int)
+    last = np.array([np.nonzero(pid == p)[0].max() for p in range(64)])
+    sub = rec[torch.from_numpy(last).cuda()].contiguous()
+    n = s.n_vars
+    x = torch.empty((n, 2, 1, 64), dtype=torch.float64, device="cuda")
+    st = torch.empty((64,), dtype=torch.int8, device="cuda")
+    t = torch.empty((64,), dtype=torch.float64, device="cuda")
+    io = ht.ht_track_io(init_records=sub.data_ptr())
+    ht.ht_track_paths_ex(ht.system_from(s, 1), s.degrees(), gam, 64, 0, None, prm, x, st, t, io=io)
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy(), full["status"])
+    assert np.array_equal(x.cpu().numpy(), full["x_end"])
+
+
+def test_features_follow_their_definition(ht):
+    from paper_1505_00383_gb300 import learned
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    prm = ht.ht_default_params(1, h_min=1e-6)
+    rec = learned.collect_records(s, 1, gam, 16, prm, stride=3)
+    f = learned.features(s, 1, prm, rec).cpu().numpy()
+    r = rec.cpu().numpy()
+    cap, n = 5, 6
+    for k in range(0, r.shape[0], 7):
+        t, h, nh = r[k, 1], r[k, 2], int(r[k, 3])
+        tv = r[k, 16:16 + cap]
+        hx = r[k, 16 + cap:].reshape(cap, n, 2, 1)
+        if nh >= 2:
+            d = hx[nh - 1, :, :, 0] - hx[nh - 2, :, :, 0]
+            dxdt = np.max(np.hypot(d[:, 0], d[:, 1])) / (tv[nh - 1] - tv[nh - 2])
+        else:
+            dxdt = 0.0
+        ref = [t, np.log10(h), np.log10(dxdt + 1e-30) / 4, np.log10(r[k, 4] + 1e-300) / 16,
+               np.log10(r[k, 5] + 1e-300) / 16, r[k, 6] / prm.newton_max, r[k, 7], nh / cap,
+               np.log10(1 - t + 1e-16) / 16]
+        ref = np.clip(ref, -4, 4)
+        assert np.allclose(f[k, :9], ref, rtol=1e-5, atol=1e-6), (k, f[k, :9], ref)
+        assert np.all(f[k, 9:] == 0)
+
+
+def test_trained_network_gains_over_the_plain_rule(ht):
+    """Train on step-start records of training systems (labels: the largest
+    step each state allowed), then track held-out systems: the learned step
+    needs fewer Newton rounds than the plain rule, with the same endpoint set
+    and the same counts of converged, failed and diverged paths."""
+    from paper_1505_00383_gb300 import learned
+    cfg = synth.CONFIGS["c3_learned_d"]
+    prm = ht.ht_default_params(1, h_min=1e-6)
+    feats, labs = [], []
+    for seed in range(cfg["train_seeds"][0], cfg["train_seeds"][0] + 6):
+        s = synth.config_system("c3_learned_d", seed)
+        gam = synth.random_gamma(seed)
+        rec = learned.collect_records(s, 1, gam, 256, prm, stride=2)
+        labs.append(learned.step_labels(s, 1, gam, prm, rec))
+        feats.append(learned.features(s, 1, prm, rec))
+    net, losses = learned.train(torch.cat(feats), torch.cat(labs), epochs=30, batch=2048, lr=2e-3)
+    assert losses[-1] < losses[0]
+    tot_plain = tot_learn = 0
+    for seed in range(cfg["heldout_seeds"][0], cfg["heldout_seeds"][0] + 2):
+        s = synth.config_system("c3_learned_d", seed)
+        gam = synth.random_gamma(seed)
+        a = learned.track(s, 1, gam, 512, prm)
+        b = learned.track(s, 1, gam, 512, prm, net=net)
+        for code in (1, -1, -2):
+            assert np.sum(a["status"] == code) == np.sum(b["status"] == code)
+        ok, worst = match_sets(to_complex(a["x_end"])[a["status"] == 1], to_complex(b["x_end"])[b["status"] == 1],
+                               1e-10)
+        assert ok, worst
+        tot_plain += a["stats"]["newton"]
+        tot_learn += b["stats"]["newton"]
+    assert tot_learn < 0.95 * tot_plain, (tot_learn, tot_plain)
