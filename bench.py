@@ -64,6 +64,24 @@ def eval_ops_per_point(system, L):
     return tot
 
 
+# Limb products (32x32 -> 64-bit multiply-adds) per complex multiplication of
+# the integer variant (paper_1505_00383_gb300/csrc/ht_mpi.cuh): 4 real
+# products, each over the limb pairs whose column is kept (x + y >= W - 2).
+INT_W = {1: 3, 2: 5, 4: 8}
+
+
+def int_products_per_point(system, L):
+    W = INT_W[L]
+    pairs = sum(1 for x in range(W) for y in range(W) if x + y >= W - 2)
+    tot = 0
+    for a in system.exps.astype(int):
+        a = a[a > 0]
+        k = a.size
+        if k:
+            tot += int((a - 1).sum()) + (1 if k == 1 else 3 * k - 3)
+    return tot * 4 * pairs
+
+
 def _args():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
@@ -141,7 +159,7 @@ def _traffic(L):
 
 def _kernel_sha():
     h = hashlib.sha256()
-    for f in ("ht_evaldiff.cu", "ht_mp.cuh"):
+    for f in ("ht_evaldiff.cu", "ht_eval.cuh", "ht_mp.cuh", "ht_mpi.cuh", "ht_mpi_eval.cuh"):
         h.update(open(os.path.join(ROOT, "paper_1505_00383_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
@@ -306,10 +324,12 @@ def run_ours(a):
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # 512 MB > L2
 
     fp64_peak = ht.ht_bench_fp64_rate(100)
-    tuned = {}
+    imad_peak = ht.ht_bench_imad_rate(20)
+    tuned, variant = {}, {}
     for L in PRECISIONS:  # autotuner: kernel body and CTA size per precision (part of warm-up)
         v, t, ms = ht.ht_tune_eval(sys_h[L], n, xs[L], vals[L], jacs[L], reps=1)
-        tuned[NAMES[L]] = {"variant": "compact" if v == 1 else "unrolled", "threads": t}
+        variant[L] = v
+        tuned[NAMES[L]] = {"variant": {0: "unrolled fp64", 1: "compact fp64", 2: "integer limbs"}[v], "threads": t}
 
     def step(events=None):
         for L in PRECISIONS:
@@ -370,19 +390,38 @@ def run_ours(a):
 
     # roofline of the dominant kernel (the one with the largest share of the step)
     dom = max(PRECISIONS, key=lambda L: statistics.mean(launch_ms[L]))
-    ops_launch = eval_ops_per_point(system, dom) * n
-    achieved = ops_launch / (statistics.mean(launch_ms[dom]) * 1e-3)
+    dom_ms = statistics.mean(launch_ms[dom])
     tr = _traffic(dom)
-    roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12,
-                "unit": "T FP64-instr/s", "frac": achieved / fp64_peak,
-                "traffic": tr, "kernel": "evaldiff_kernel<%d> (%s)" % (dom, NAMES[dom]),
-                "peak_source": "measured live: ht_bench_fp64_rate (DFMA chains on all SMs)"}
+    if variant[dom] == 2:
+        work = int_products_per_point(system, dom) * n
+        achieved = work / (dom_ms * 1e-3)
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_peak / 1e12,
+                    "unit": "T IMAD.WIDE/s", "frac": achieved / imad_peak, "traffic": tr,
+                    "kernel": "evaldiff_int_kernel<%d> (%s, integer limbs)" % (dom, NAMES[dom]),
+                    "work": "32x32->64-bit limb products of the complex multiplications",
+                    "peak_source": "measured live: ht_bench_imad_rate (IMAD.WIDE chains on all SMs)"}
+    else:
+        ops_launch = eval_ops_per_point(system, dom) * n
+        achieved = ops_launch / (dom_ms * 1e-3)
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": fp64_peak / 1e12,
+                    "unit": "T FP64-instr/s", "frac": achieved / fp64_peak,
+                    "traffic": tr, "kernel": "evaldiff_kernel<%d> (%s)" % (dom, NAMES[dom]),
+                    "work": "FP64 instructions of the error-free DD/QD arithmetic",
+                    "peak_source": "measured live: ht_bench_fp64_rate (DFMA chains on all SMs)"}
     per_prec = {}
     for L in PRECISIONS:
         m = statistics.mean(launch_ms[L])
-        ops = eval_ops_per_point(system, L) * n
-        per_prec[NAMES[L]] = {"ms": m, "pts_per_s": n / (m * 1e-3), "fp64_frac": ops / (m * 1e-3) / fp64_peak,
-                              "out_GB_per_s": (system.n_polys * (system.n_vars + 1) * 16 * L * n) / (m * 1e-3) / 1e9}
+        d = {"ms": m, "pts_per_s": n / (m * 1e-3), "variant": tuned[NAMES[L]]["variant"],
+             "out_GB_per_s": (system.n_polys * (system.n_vars + 1) * 16 * L * n) / (m * 1e-3) / 1e9}
+        if variant[L] == 2:
+            d["imad_frac"] = int_products_per_point(system, L) * n / (m * 1e-3) / imad_peak
+        else:
+            d["fp64_frac"] = eval_ops_per_point(system, L) * n / (m * 1e-3) / fp64_peak
+        per_prec[NAMES[L]] = d
+    peaks = {"fp64_instr_per_s": fp64_peak, "imad_wide_per_s": imad_peak}
+    mp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(mp):
+        peaks["hbm_GBps_measured"] = json.load(open(mp)).get("hbm_gbs")
 
     tracking = {}
     for name in [w for w in a.track.split(",") if w]:
@@ -407,7 +446,7 @@ def run_ours(a):
                        "monomial_vars": "2-8", "exponents": "1-3", "n_pts_per_gpu": n,
                        "l2": "flushed (512 MB write) before every timed step; outputs 1.1-4.5 GB per launch",
                        "parallelism": "independent batch per GPU"},
-            "per_precision": per_prec, "tuned": tuned, "tracking": tracking, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "per_precision": per_prec, "tuned": tuned, "tracking": tracking, "roofline": roofline, "peaks": peaks, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": a.steps * len(PRECISIONS), "clocks": clk.summary(),
             "wall_s_timed_region": t_wall,
         }))

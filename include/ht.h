@@ -112,10 +112,18 @@ int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, doubl
 /*
  * ht_set_eval_config -- choose how ht_eval_diff runs on this system:
  *   variant  1 compact monomial bodies (one code path for every support size),
- *            0 unrolled bodies for supports of up to 8 variables, -1 default (1)
- *   threads  CTA size 64, 128 or 256, or 0 for the default (128)
- * Both variants perform the same operations in the same order, so results do
- * not depend on the choice; only the speed does.
+ *            0 unrolled bodies for supports of up to 8 variables,
+ *            2 integer limbs: the complex products on the integer pipe in
+ *              radix-2^29 limbs, sums in an exact fixed-point frame per
+ *              output (systems with at most 64 variables; HT_EUNSUPPORTED
+ *              otherwise),
+ *           -1 default (1)
+ *   threads  CTA size 64, 128 or 256, or 0 for the default (128); variant 2
+ *            always runs 128-thread CTAs
+ * Variants 0 and 1 perform the same operations in the same order, so their
+ * results are bitwise identical; variant 2 meets the same accuracy bound
+ * (a small multiple of 2^(-53 L) times the sum of the moduli of the terms of
+ * each output) with its own rounding.
  */
 int ht_set_eval_config(ht_system* sys, int variant, int threads);
 
@@ -123,7 +131,8 @@ int ht_set_eval_config(ht_system* sys, int variant, int threads);
  * ht_tune_eval -- autotuner for ht_eval_diff: times every (variant, threads)
  * configuration on the given device buffers (reps timed launches each, CUDA
  * events on `stream`), keeps the fastest in the system and reports it (any
- * output pointer may be NULL).  Overwrites val and jac.  Blocks.
+ * output pointer may be NULL).  On return val and jac hold the chosen
+ * configuration's results.  Blocks.
  */
 int ht_tune_eval(ht_system* sys, int64_t n_pts, const double* x, double* val, double* jac, int reps, int* variant,
                  int* threads, float* best_ms, void* stream);

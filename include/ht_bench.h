@@ -25,6 +25,14 @@ extern "C" {
  */
 int ht_bench_fp64_rate(int iters, double* ops_per_s, void* stream);
 
+/*
+ * ht_bench_imad_rate -- throughput of 32 x 32 -> 64-bit integer multiply-adds
+ * (IMAD.WIDE, the limb product of the integer evaluation variant) on the
+ * current device, in lane operations per second, measured like
+ * ht_bench_fp64_rate.
+ */
+int ht_bench_imad_rate(int iters, double* ops_per_s, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -4,7 +4,10 @@
 #include <cstring>
 #include <string>
 
+#include <cmath>
+
 #include "ht_internal.h"
+#include "ht_mpi.cuh"
 
 namespace ht {
 
@@ -144,6 +147,43 @@ int ht_create_system(int n_vars, int n_polys, const int32_t* n_terms, const int8
     delete s;
     return cuda_fail(e, "ht_create_system: upload");
   }
+  // integer-format coefficients for the integer evaluation variant
+  {
+    const size_t zsz = limbs == 1 ? sizeof(mpi::fz<3>) : (limbs == 2 ? sizeof(mpi::fz<5>) : sizeof(mpi::fz<8>));
+    std::vector<unsigned char> hz((size_t)s->M * zsz);
+    std::vector<float> hl(s->M);
+    for (int64_t m = 0; m < s->M; ++m) {
+      const double* re = coef + m * 2 * limbs;
+      const double* im = re + limbs;
+      if (limbs == 1) {
+        mpi::fz<3> z = mpi::from_doubles<3, 1>(re, im);
+        std::memcpy(&hz[m * zsz], &z, zsz);
+      } else if (limbs == 2) {
+        mpi::fz<5> z = mpi::from_doubles<5, 2>(re, im);
+        std::memcpy(&hz[m * zsz], &z, zsz);
+      } else {
+        mpi::fz<8> z = mpi::from_doubles<8, 4>(re, im);
+        std::memcpy(&hz[m * zsz], &z, zsz);
+      }
+      const double mod = std::hypot(re[0], im[0]);
+      hl[m] = mod == 0.0 ? -1000.0f : (float)std::log2(mod);
+    }
+    void* blk = nullptr;
+    e = cudaMalloc(&blk, hz.size() + hl.size() * sizeof(float) + 256);
+    if (e == cudaSuccess) {
+      s->d_coef_fz = blk;
+      s->d_coef_lg = (float*)((char*)blk + ((hz.size() + 255) & ~(size_t)255));
+      e = cudaMemcpy(s->d_coef_fz, hz.data(), hz.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(s->d_coef_lg, hl.data(), hl.size() * sizeof(float), cudaMemcpyHostToDevice);
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (s->d_coef_fz) cudaFree(s->d_coef_fz);
+      cudaFree(s->d_block);
+      delete s;
+      return set_error(HT_ENOMEM, "ht_create_system: integer coefficients");
+    }
+  }
   *out = s;
   return HT_OK;
 }
@@ -155,6 +195,7 @@ int ht_destroy_system(ht_system* s) {
   if (s->d_block) cudaFree(s->d_block);
   if (s->d_ws) cudaFree(s->d_ws);
   if (s->d_track_ws) cudaFree(s->d_track_ws);
+  if (s->d_coef_fz) cudaFree(s->d_coef_fz);
   if (s->h_count) cudaFreeHost(s->h_count);
   for (auto& g : s->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
@@ -241,7 +282,9 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
 int ht_set_eval_config(ht_system* s, int variant, int threads) {
   clear_error();
   if (!s) return set_error(HT_EINVAL, "ht_set_eval_config: NULL system");
-  if (variant < -1 || variant > 1) return set_error(HT_EINVAL, "ht_set_eval_config: variant=%d", variant);
+  if (variant < -1 || variant > 2) return set_error(HT_EINVAL, "ht_set_eval_config: variant=%d", variant);
+  if (variant == 2 && s->nv > 64)
+    return set_error(HT_EUNSUPPORTED, "ht_set_eval_config: the integer variant supports at most 64 variables");
   if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
     return set_error(HT_EINVAL, "ht_set_eval_config: threads=%d (0, 64, 128 or 256)", threads);
   s->eval_variant = variant;
@@ -259,11 +302,13 @@ int ht_tune_eval(ht_system* s, int64_t n_pts, const double* x, double* val, doub
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int variants[2] = {1, 0}, sizes[3] = {128, 64, 256};
+  const int variants[3] = {1, 0, 2}, sizes[3] = {128, 64, 256};
+  const int nvar = s->nv <= 64 ? 3 : 2;
   float best = 1e30f;
   int bv = 1, bt = 128;
-  for (int vi = 0; vi < 2 && rc == HT_OK; ++vi)
+  for (int vi = 0; vi < nvar && rc == HT_OK; ++vi)
     for (int ti = 0; ti < 3 && rc == HT_OK; ++ti) {
+      if (variants[vi] == 2 && ti > 0) continue;  // one CTA size for the integer variant
       s->eval_variant = variants[vi];
       s->eval_threads = sizes[ti];
       rc = launch_evaldiff(s, n_pts, x, val, jac, st);  // warm-up
@@ -284,6 +329,12 @@ int ht_tune_eval(ht_system* s, int64_t n_pts, const double* x, double* val, doub
   cudaEventDestroy(e1);
   s->eval_variant = bv;
   s->eval_threads = bt;
+  // leave the chosen configuration's results in val and jac
+  if (rc == HT_OK) rc = launch_evaldiff(s, n_pts, x, val, jac, st);
+  if (rc == HT_OK) {
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "ht_tune_eval");
+  }
   if (variant) *variant = bv;
   if (threads) *threads = bt;
   if (best_ms) *best_ms = best;

@@ -25,6 +25,8 @@ struct ht_system {
   int32_t* d_mon_off = nullptr;  // [M + 1] range of each monomial in d_pairs
   uint16_t* d_pairs = nullptr;   // variable | exponent << 8, variables increasing
   double* d_coef = nullptr;      // [M][2][L]
+  void* d_coef_fz = nullptr;     // [M] coefficients in the integer format (L = 2, 4)
+  float* d_coef_lg = nullptr;    // [M] log2 |c| (-1000 for zero)
   void* d_ws = nullptr;          // workspace for the host-buffer entry points
   size_t ws_bytes = 0;
   void* d_track_ws = nullptr;    // per-path tracker state (grown on demand)

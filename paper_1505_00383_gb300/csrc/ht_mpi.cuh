@@ -1,0 +1,371 @@
+// Multi-limb integer complex arithmetic for the evaluation kernel.
+//
+// GB300's FP64 pipe issues one warp instruction per 64 clocks per SM
+// sub-partition, 30 to 60 times less than its integer multiply-add pipe.  The
+// double double and quad double products that dominate evaluation are
+// therefore computed here on the integer pipe, with the same accuracy contract
+// (error a small multiple of 2^(-53 L) times the sum of the moduli of the
+// terms):
+//
+//   * a floating complex number fz<W> holds re and im as W signed limbs of
+//     radix 2^29 sharing one binary exponent: value = sum_k d_k 2^(29 k + f);
+//     limbs 0..W-2 lie in [0, 2^29), the top limb is signed;
+//   * a product of two fz<W> accumulates the 32x32 -> 64-bit limb products
+//     column by column in 64-bit integers (columns below W-2 are dropped: they
+//     are below the result's last limb), propagates carries, and keeps the W
+//     limbs from the highest nonzero column down -- at least 29 (W - 1) + 1
+//     significant bits, and the magnitude of a complex product never cancels;
+//   * sums are exact integer additions in a fixed-point frame chosen per
+//     polynomial and point from a rigorous bound on the terms (fixed<WA>), so
+//     accumulation needs neither alignment nor normalisation;
+//   * conversions from and to L-limb doubles are exact up to the last limb.
+//
+// Everything is host+device so the host can test the same code.
+#pragma once
+#include <cstdint>
+#include <cstring>
+
+#if defined(__CUDACC__)
+#define HT_HD __host__ __device__ __forceinline__
+#else
+#define HT_HD inline
+#endif
+
+namespace ht {
+namespace mpi {
+
+constexpr int RB = 29;
+constexpr int32_t MASK = (1 << RB) - 1;
+
+template <int W>
+struct fz {
+  int32_t f;  // binary exponent of limb 0's lowest bit
+  int32_t r[W], i[W];
+};
+
+HT_HD int64_t dbits(double d) {
+  int64_t b;
+  std::memcpy(&b, &d, 8);
+  return b;
+}
+HT_HD double bitsd(int64_t b) {
+  double d;
+  std::memcpy(&d, &b, 8);
+  return d;
+}
+// Decompose a finite double into (signed 53-bit integer m, exponent q): d = m 2^q.
+// Zero gives m = 0.  (Subnormals are handled exactly as well.)
+HT_HD void decompose(double d, int64_t& m, int& q) {
+  const int64_t b = dbits(d);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  int64_t mant = b & ((1LL << 52) - 1);
+  if (ex == 0) {
+    q = -1074;
+  } else {
+    mant |= (1LL << 52);
+    q = ex - 1075;
+  }
+  m = (b < 0) ? -mant : mant;
+}
+// floor(log2 |d|) of a nonzero double (normals; subnormals treated as 2^-1023)
+HT_HD int ilog2(double d) {
+  const int ex = (int)((dbits(d) >> 52) & 0x7ff);
+  return ex == 0 ? -1023 : ex - 1023;
+}
+
+// Add the signed integer m * 2^q into column sums acc[0..N) whose column k has
+// weight 2^(29 k + f); bits below column 0 are dropped.  |m| < 2^53.
+template <int N>
+HT_HD void add_scaled(int64_t* acc, int64_t m, int q, int f) {
+  if (m == 0) return;
+  const bool neg = m < 0;
+  uint64_t a = (uint64_t)(neg ? -m : m);
+  int s = q - f;  // bit position of m's lowest bit in the frame
+  if (s < 0) {
+    if (-s >= 64) return;
+    a >>= -s;
+    s = 0;
+  }
+  int k = s / RB, r = s % RB;
+  // a (< 2^53) shifted left by r (< 29) spans up to 82 bits: split in 29-bit pieces
+  uint64_t lo = a & (uint64_t)MASK;      // bits 0..28
+  uint64_t hi = a >> RB;                 // bits 29..52 (< 2^24)
+  uint64_t p0 = lo << r;                 // < 2^57
+  uint64_t p1 = hi << r;                 // < 2^52
+  int64_t c0 = (int64_t)(p0 & MASK), c1 = (int64_t)((p0 >> RB) + (p1 & MASK)), c2 = (int64_t)(p1 >> RB);
+  if (neg) {
+    c0 = -c0;
+    c1 = -c1;
+    c2 = -c2;
+  }
+#pragma unroll
+  for (int j = 0; j < N; ++j) {
+    if (j == k) acc[j] += c0;
+    if (j == k + 1) acc[j] += c1;
+    if (j == k + 2) acc[j] += c2;
+  }
+}
+
+// Carry-propagate column sums into limbs: limbs 0..N-2 in [0, 2^29), the top
+// limb signed (it absorbs the final carry).
+template <int N>
+HT_HD void carry(int64_t* acc) {
+#pragma unroll
+  for (int j = 0; j + 1 < N; ++j) {
+    const int64_t c = acc[j] >> RB;  // floor division (arithmetic shift)
+    acc[j] -= c << RB;
+    acc[j + 1] += c;
+  }
+}
+
+// From L doubles per component (unevaluated sums; limb 0 leading).  The frame
+// puts the leading bit of the larger component at bit 27 of the top limb.
+template <int W, int L>
+HT_HD fz<W> from_doubles(const double* re, const double* im) {
+  fz<W> z;
+  const double r0 = re[0], i0 = im[0];
+  int e;
+  if (r0 == 0.0 && i0 == 0.0) {
+    e = 0;
+  } else if (r0 == 0.0) {
+    e = ilog2(i0);
+  } else if (i0 == 0.0) {
+    e = ilog2(r0);
+  } else {
+    const int a = ilog2(r0), b = ilog2(i0);
+    e = a > b ? a : b;
+  }
+  z.f = e - 27 - RB * (W - 1);
+  int64_t ar[W], ai[W];
+#pragma unroll
+  for (int k = 0; k < W; ++k) ar[k] = ai[k] = 0;
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    int64_t m;
+    int q;
+    decompose(re[l], m, q);
+    add_scaled<W>(ar, m, q, z.f);
+    decompose(im[l], m, q);
+    add_scaled<W>(ai, m, q, z.f);
+  }
+  carry<W>(ar);
+  carry<W>(ai);
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    z.r[k] = (int32_t)ar[k];
+    z.i[k] = (int32_t)ai[k];
+  }
+  return z;
+}
+
+// Complex product.  Columns W-2 .. 2W-1 of the exact limb product (the lower
+// ones only feed a carry below the result's last limb and are dropped).
+template <int W>
+HT_HD fz<W> mul(const fz<W>& a, const fz<W>& b) {
+  constexpr int C0 = W - 2 > 0 ? W - 2 : 0;  // lowest column kept
+  constexpr int NC = 2 * W - C0;             // columns C0 .. 2W-1
+  int64_t cr[NC], ci[NC], cr2[NC], ci2[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) cr[c] = ci[c] = cr2[c] = ci2[c] = 0;
+#pragma unroll
+  for (int x = 0; x < W; ++x)
+#pragma unroll
+    for (int y = 0; y < W; ++y) {
+      if (x + y < C0) continue;
+      const int c = x + y - C0;
+      cr[c] += (int64_t)a.r[x] * b.r[y];
+      cr2[c] += (int64_t)a.i[x] * b.i[y];
+      ci[c] += (int64_t)a.r[x] * b.i[y];
+      ci2[c] += (int64_t)a.i[x] * b.r[y];
+    }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    cr[c] -= cr2[c];
+    ci[c] += ci2[c];
+  }
+  carry<NC>(cr);
+  carry<NC>(ci);
+  // window: columns [W-1, 2W-2] if the top column is only a sign, else [W, 2W-1]
+  const int64_t tr = cr[NC - 1], ti = ci[NC - 1];
+  const bool high = !((tr == 0 || tr == -1) && (ti == 0 || ti == -1));
+  fz<W> z;
+  if (high) {
+    z.f = a.f + b.f + RB * W;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      z.r[k] = (int32_t)cr[k + W - C0];
+      z.i[k] = (int32_t)ci[k + W - C0];
+    }
+  } else {
+    z.f = a.f + b.f + RB * (W - 1);
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      z.r[k] = (int32_t)cr[k + W - 1 - C0];
+      z.i[k] = (int32_t)ci[k + W - 1 - C0];
+    }
+    z.r[W - 1] += (int32_t)(tr * (1LL << RB));  // fold a sign-only top column
+    z.i[W - 1] += (int32_t)(ti * (1LL << RB));
+  }
+  return z;
+}
+
+// Add e * z (e a small positive integer) into fixed-point accumulators with
+// limb 0 weight 2^F: acc_r, acc_i [WA] int32 (limbs 0..WA-2 in [0, 2^29) after
+// the carry, top signed).  The caller guarantees |e z| < 2^(29 (WA - 1) + 28 + F)
+// (returns false, adding nothing, if z's frame lies above the accumulator's).
+template <int W, int WA>
+HT_HD bool acc_add(int32_t* acc_r, int32_t* acc_i, const fz<W>& z, int e, int F) {
+  const int s = F - z.f;  // right shift of z into the accumulator frame
+  if (s < -(RB - 1)) return false;
+  int64_t ar[WA], ai[WA];
+#pragma unroll
+  for (int k = 0; k < WA; ++k) {
+    ar[k] = acc_r[k];
+    ai[k] = acc_i[k];
+  }
+  // z = sum_k d_k 2^(29 k + f): add each limb as a scaled integer
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    add_scaled<WA>(ar, (int64_t)z.r[k] * e, z.f + RB * k, F);
+    add_scaled<WA>(ai, (int64_t)z.i[k] * e, z.f + RB * k, F);
+  }
+  carry<WA>(ar);
+  carry<WA>(ai);
+#pragma unroll
+  for (int k = 0; k < WA; ++k) {
+    acc_r[k] = (int32_t)ar[k];
+    acc_i[k] = (int32_t)ai[k];
+  }
+  return true;
+}
+
+// One component of e * z added into fixed-point column sums acc[WA] (limb 0
+// weight 2^F), by one shift of the whole two's complement limb string: limb k
+// of z sits at bit 29 k + (f - F) of the accumulator frame.  Bits that land
+// below limb 0 are dropped (truncation: at most one unit of the last limb).
+// -28 <= f - F required above the frame's top (the caller's bound).
+template <int W, int WA>
+HT_HD void add_shifted_comp(int64_t* acc, const int32_t* z, int s, int e) {
+  // s = F - f: right shift in bits (may be slightly negative: left shift)
+  int32_t D[W + WA + 3];
+  const int32_t ext = z[W - 1] < 0 ? MASK : 0;
+#pragma unroll
+  for (int k = 0; k < W - 1; ++k) D[k] = z[k];
+  D[W - 1] = z[W - 1] & MASK;
+#pragma unroll
+  for (int k = W; k < W + WA + 3; ++k) D[k] = ext;
+  if (s >= 0) {
+    const int q = s / RB, r = s % RB;
+    if (q >= W) {
+      return;  // below the accumulator's last limb
+    }
+#pragma unroll
+    for (int j = 0; j < WA; ++j) {
+      const int32_t lo = D[j + q], hi = D[j + q + 1];
+      int32_t v = r == 0 ? lo : (int32_t)((((uint32_t)lo >> r) | ((uint32_t)hi << (RB - r))) & (uint32_t)MASK);
+      if (j == WA - 1) v = (v << (32 - RB)) >> (32 - RB);  // the top limb carries the sign
+      acc[j] += (int64_t)e * v;
+    }
+  } else {
+    const int u = -s;  // 1..28
+#pragma unroll
+    for (int j = 0; j < WA; ++j) {
+      const int32_t lo = j > 0 ? D[j - 1] : 0, hi = D[j];
+      int32_t v = (int32_t)((((uint32_t)hi << u) | ((uint32_t)lo >> (RB - u))) & (uint32_t)MASK);
+      if (j == WA - 1) v = (v << (32 - RB)) >> (32 - RB);
+      acc[j] += (int64_t)e * v;
+    }
+  }
+}
+
+// e * z into int32 accumulators acc_r, acc_i [WA] (frame F), carried.
+// Returns false (adding nothing) if z's frame lies more than 28 bits above F.
+template <int W, int WA>
+HT_HD bool acc_add_fast(int32_t* acc_r, int32_t* acc_i, const fz<W>& z, int e, int F) {
+  const int s = F - z.f;
+  if (s < -(RB - 1)) return false;
+  int64_t ar[WA], ai[WA];
+#pragma unroll
+  for (int k = 0; k < WA; ++k) {
+    ar[k] = acc_r[k];
+    ai[k] = acc_i[k];
+  }
+  add_shifted_comp<W, WA>(ar, z.r, s, e);
+  add_shifted_comp<W, WA>(ai, z.i, s, e);
+  carry<WA>(ar);
+  carry<WA>(ai);
+#pragma unroll
+  for (int k = 0; k < WA; ++k) {
+    acc_r[k] = (int32_t)ar[k];
+    acc_i[k] = (int32_t)ai[k];
+  }
+  return true;
+}
+
+// Fixed-point value sum_k a_k 2^(29 k + F) (WA limbs, top signed) to L doubles
+// whose sum equals it up to the last double's precision: the magnitude's bits
+// are cut from the top into 53-bit pieces (each piece exact in a double).
+template <int WA, int L>
+HT_HD void fixed_to_doubles(const int32_t* a, int F, double* out) {
+  int64_t m[WA];
+#pragma unroll
+  for (int k = 0; k < WA; ++k) m[k] = a[k];
+  carry<WA>(m);
+  const bool neg = m[WA - 1] < 0;
+  if (neg) {
+#pragma unroll
+    for (int k = 0; k < WA; ++k) m[k] = -m[k];
+    carry<WA>(m);  // magnitude: all limbs in [0, 2^29), top >= 0
+  }
+  // top nonzero limb and bit
+  int top = -1;
+#pragma unroll
+  for (int k = 0; k < WA; ++k)
+    if (m[k] != 0) top = k;
+#pragma unroll
+  for (int l = 0; l < L; ++l) out[l] = 0.0;
+  if (top < 0) return;
+  int tb = 0;
+  {
+    uint64_t v = (uint64_t)m[top];
+    while (v >> (tb + 1)) ++tb;
+  }
+  int hi_bit = RB * top + tb;  // absolute bit index of the leading bit
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    // extract bits [hi_bit - 52, hi_bit] as an integer (bits below 0 are zero)
+    const int lo_bit = hi_bit - 52;
+    uint64_t piece = 0;
+#pragma unroll
+    for (int k = 0; k < WA; ++k) {
+      const int base = RB * k;  // limb k covers bits [base, base + 28]
+      if (base + RB - 1 < lo_bit || base > hi_bit) continue;
+      uint64_t v = (uint64_t)m[k];
+      // keep the part of limb k inside [lo_bit, hi_bit]
+      int from = lo_bit > base ? lo_bit - base : 0;
+      int to = hi_bit < base + RB - 1 ? hi_bit - base : RB - 1;
+      v = (v >> from) & ((1ULL << (to - from + 1)) - 1);
+      const int pos = base + from - lo_bit;  // position in the piece
+      piece |= pos >= 0 ? (v << pos) : (v >> -pos);
+    }
+    // piece * 2^(lo_bit + F), exact (piece < 2^53)
+    double d = (double)(int64_t)piece;
+    int ex = lo_bit + F;
+    // scale by 2^ex in steps that stay in range
+    while (ex > 600) {
+      d *= bitsd((int64_t)(1023 + 600) << 52);
+      ex -= 600;
+    }
+    while (ex < -600) {
+      d *= bitsd((int64_t)(1023 - 600) << 52);
+      ex += 600;
+    }
+    d *= bitsd((int64_t)(1023 + ex) << 52);
+    out[l] = neg ? -d : d;
+    hi_bit = lo_bit - 1;
+    if (hi_bit < 0) break;
+  }
+}
+
+}  // namespace mpi
+}  // namespace ht

@@ -51,6 +51,7 @@ SIGNATURES = {
     "ht_step_labels": ([P, P, P, P, I64, P, I32, P, I32, P, P], I32),
     "ht_step_features": ([I32, I32, I32, I32, I64, P, P, P], I32),
     "ht_bench_fp64_rate": ([I32, ctypes.POINTER(ctypes.c_double), P], I32),
+    "ht_bench_imad_rate": ([I32, ctypes.POINTER(ctypes.c_double), P], I32),
 }
 
 
@@ -207,6 +208,13 @@ def ht_bench_fp64_rate(iters: int = 50, stream=None) -> float:
     """Measured FP64 instructions per second of the current device."""
     r = ctypes.c_double()
     _check(lib().ht_bench_fp64_rate(iters, ctypes.byref(r), _stream(stream)))
+    return r.value
+
+
+def ht_bench_imad_rate(iters: int = 20, stream=None) -> float:
+    """Measured 32x32->64-bit integer multiply-adds per second of the device."""
+    r = ctypes.c_double()
+    _check(lib().ht_bench_imad_rate(iters, ctypes.byref(r), _stream(stream)))
     return r.value
 
 

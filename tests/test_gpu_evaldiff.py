@@ -146,5 +146,65 @@ def test_every_kernel_configuration_gives_identical_results(ht, L):
     val = torch.empty((s.n_polys, 2, L, n), dtype=torch.float64, device="cuda")
     jac = torch.empty((s.n_polys, s.n_vars, 2, L, n), dtype=torch.float64, device="cuda")
     v, t, ms = ht.ht_tune_eval(hs, n, xd, val, jac, reps=1)
-    assert v in (0, 1) and t in (64, 128, 256) and ms > 0
-    assert np.array_equal(val.cpu().numpy(), ref[0])
+    assert v in (0, 1, 2) and t in (64, 128, 256) and ms > 0
+    if v in (0, 1):
+        assert np.array_equal(val.cpu().numpy(), ref[0])
+    else:  # the integer variant: its own arithmetic, same accuracy contract
+        _check(s, x, L, val.cpu().numpy(), jac.cpu().numpy())
+
+
+def _run_variant(ht, system, x, L, variant):
+    nv, _, _, n = x.shape
+    hs = ht.system_from(system, L)
+    ht.ht_set_eval_config(hs, variant, 0)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    val = torch.full((system.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    jac = torch.full((system.n_polys, nv, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    ht.ht_eval_diff(hs, n, xd, val, jac)
+    torch.cuda.synchronize()
+    return val.cpu().numpy(), jac.cpu().numpy()
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("name", ["c0_plain_d", "c2_batched_dd", "c4_stress_qd", "c1_evaldiff"])
+def test_integer_variant_matches_oracle(ht, name, L):
+    """The integer-pipe evaluation (multi-limb integer complex arithmetic with
+    fixed-point accumulation) meets the same tolerance against the oracle."""
+    s = synth.config_system(name)
+    n = 32 * 3 + 5
+    if name == "c1_evaldiff" and L == 4:
+        n = 32 + 3
+    x = synth.unit_points(201 + L, s.n_vars, n, L)
+    val, jac = _run_variant(ht, s, x, L, 2)
+    _check(s, x, L, val, jac)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_integer_variant_full_size_sampled(ht, L):
+    s = synth.config_system("c1_evaldiff")
+    n = 65536
+    x = synth.unit_points(3000 + L, s.n_vars, n, L)
+    val, jac = _run_variant(ht, s, x, L, 2)
+    rng = synth.SplitMix64(19 + L)
+    pts = np.unique(np.concatenate([[0, 31, 32, n - 1], rng.integers(0, n - 1, {1: 12, 2: 6, 4: 2}[L])]))
+    _check(s, x, L, val, jac, pts=pts)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_integer_variant_edge_cases(ht, L):
+    """Constant terms, a 12-variable support, exponent 9, values spread over
+    many binades and exact zeros among the inputs."""
+    nv = 12
+    exps = np.zeros((5, nv), np.int8)
+    exps[1, :] = 1
+    exps[2, 3] = 9
+    exps[3, [0, 5, 11]] = [2, 3, 1]
+    exps[4, 7] = 1
+    coef = np.array([[0.5, -0.25], [1.0, 0.0], [-0.3, 0.7], [0.2, 0.2], [0.0, 1.0]])
+    s = synth.System(nv, 2, np.array([3, 2], np.int32), exps, coef)
+    x = synth.unit_points(8, nv, 40, L)
+    rng = synth.SplitMix64(4)
+    x *= 2.0 ** rng.integers(-20, 20, nv * 40).reshape(nv, 1, 1, 40).astype(np.float64)
+    x[2, :, :, 5] = 0.0   # an exact zero variable at one point
+    val, jac = _run_variant(ht, s, x, L, 2)
+    _check(s, x, L, val, jac)

@@ -1,0 +1,218 @@
+"""CPU tests of the library's multi-limb integer complex arithmetic
+(csrc/ht_mpi.cuh, compiled for the host): conversions, products and
+fixed-point accumulation against the oracle's exact L-limb arithmetic."""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import pytest
+
+import synth
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+@pytest.fixture(scope="module")
+def shim(tmp_path_factory):
+    out = str(tmp_path_factory.mktemp("mpi") / "libmpi_shim.so")
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-fPIC", "-shared", "-o", out, os.path.join(HERE, "mpi_shim.cpp")])
+    L = ctypes.CDLL(out)
+    P, I64 = ctypes.c_void_p, ctypes.c_int64
+    L.mpi_roundtrip.argtypes = [ctypes.c_int, I64, P, P]
+    L.mpi_product.argtypes = [ctypes.c_int, I64, P, P, ctypes.c_int, P]
+    L.mpi_dot.argtypes = [ctypes.c_int, I64, ctypes.c_int, P, P, P, ctypes.c_int, P]
+    L.mpi_dot_fast.argtypes = [ctypes.c_int, I64, ctypes.c_int, P, P, P, ctypes.c_int, P]
+    return L
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _complex(seed, n, L, spread=30):
+    rng = synth.SplitMix64(seed)
+    re, im = synth.unit_circle(rng, n)
+    scale = 2.0 ** rng.integers(-spread, spread, n).astype(np.float64)
+    out = np.empty((n, 2, L))
+    out[:, 0, :] = synth.random_tails(rng, re * scale, L).T
+    out[:, 1, :] = synth.random_tails(rng, im * scale, L).T
+    out[:7, 1, :] = 0.0  # purely real values
+    out[7:12, 0, :] = -out[7:12, 0, :]
+    return np.ascontiguousarray(out)
+
+
+def _cerr(oracle_lib, got, ref):
+    d = [oracle_lib.value_diff(got[:, c, :], ref[:, c, :]) for c in (0, 1)]
+    return np.hypot(d[0], d[1])
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_conversion_round_trip(oracle_lib, shim, L):
+    x = _complex(1 + L, 500, L)
+    out = np.empty_like(x)
+    assert shim.mpi_roundtrip(L, x.shape[0], _p(x), _p(out)) == 0
+    mag = np.hypot(x[:, 0, 0], x[:, 1, 0])
+    err = _cerr(oracle_lib, out, x)
+    assert np.all(err <= 2.0 ** (-53 * L + 3) * mag), np.max(err / mag)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+@pytest.mark.parametrize("e", [1, 3])
+def test_product_against_oracle(oracle_lib, shim, L, e):
+    """e * (a * b) against the oracle's complex product (each real operation
+    rounded to L limbs) within a few units of 2^(-53 L) of |a| |b|."""
+    n = 400
+    a = _complex(10 + L, n, L)
+    b = _complex(20 + L, n, L)
+    out = np.empty_like(a)
+    assert shim.mpi_product(L, n, _p(a), _p(b), e, _p(out)) == 0
+    ar, ai = a[:, 0, :], a[:, 1, :]
+    br, bi = b[:, 0, :], b[:, 1, :]
+    mul = lambda u, v: oracle_lib.real_op("mul", u, v)
+    add = lambda u, v: oracle_lib.real_op("add", u, v)
+    sub = lambda u, v: oracle_lib.real_op("sub", u, v)
+    ref = np.empty_like(a)
+    ref[:, 0, :] = sub(mul(ar, br), mul(ai, bi))
+    ref[:, 1, :] = add(mul(ar, bi), mul(ai, br))
+    ee = np.zeros((n, L))
+    ee[:, 0] = e
+    ref[:, 0, :] = mul(ref[:, 0, :], ee)
+    ref[:, 1, :] = mul(ref[:, 1, :], ee)
+    scale = e * np.hypot(ar[:, 0], ai[:, 0]) * np.hypot(br[:, 0], bi[:, 0])
+    err = _cerr(oracle_lib, out, ref)
+    assert np.all(err <= 2.0 ** (-53 * L + 5) * scale), np.max(err / scale)
+
+
+@pytest.mark.parametrize("fast", [False, True])
+@pytest.mark.parametrize("L", [2, 4])
+def test_fixed_point_sums_with_cancellation(oracle_lib, shim, L, fast):
+    """sum_j e_j a_j b_j in one fixed-point frame, with headroom bits, against
+    the oracle: error relative to sum_j e_j |a_j b_j| (condition-aware)."""
+    n, k = 60, 24
+    a = _complex(30 + L, n * k, L, spread=8).reshape(n, k, 2, L)
+    b = _complex(40 + L, n * k, L, spread=8).reshape(n, k, 2, L)
+    a[:, 1] = -a[:, 0] * 1.0  # strong cancellation between the first two terms
+    b[:, 1] = b[:, 0]
+    e = np.array([1 + (j % 3) for j in range(k)], dtype=np.int32)
+    out = np.empty((n, 2, L))
+    fn = shim.mpi_dot_fast if fast else shim.mpi_dot
+    assert fn(L, n, k, _p(np.ascontiguousarray(a)), _p(np.ascontiguousarray(b)), _p(e), 6, _p(out)) == 0
+    mul = lambda u, v: oracle_lib.real_op("mul", u, v)
+    add = lambda u, v: oracle_lib.real_op("add", u, v)
+    sub = lambda u, v: oracle_lib.real_op("sub", u, v)
+    ref = np.zeros((n, 2, L))
+    absum = np.zeros(n)
+    for j in range(k):
+        ar, ai, br, bi = a[:, j, 0], a[:, j, 1], b[:, j, 0], b[:, j, 1]
+        ee = np.zeros((n, L))
+        ee[:, 0] = e[j]
+        tr = mul(sub(mul(ar, br), mul(ai, bi)), ee)
+        ti = mul(add(mul(ar, bi), mul(ai, br)), ee)
+        ref[:, 0] = add(ref[:, 0], tr)
+        ref[:, 1] = add(ref[:, 1], ti)
+        absum += e[j] * np.hypot(ar[:, 0], ai[:, 0]) * np.hypot(br[:, 0], bi[:, 0])
+    err = _cerr(oracle_lib, out, ref)
+    assert np.all(err <= 2.0 ** (-53 * L + 12) * absum), np.max(err / absum)
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_shift_accumulation_equals_generic(shim, L):
+    """The single-shift accumulation gives the same limbs as the generic
+    per-limb one for right and left shifts (frames slightly above the
+    accumulator's included)."""
+    shim.mpi_compare_acc.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    shim.mpi_compare_acc.restype = ctypes.c_int64
+    x = _complex(77 + L, 200, L, spread=3)
+    worst = shim.mpi_compare_acc(L, x.shape[0], _p(x), -20, 29 * 9)
+    assert 0 <= worst <= 2 * 8, worst  # within a few units of the last limb
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("name", ["c0_plain_d", "c2_batched_dd", "c4_stress_qd", "c1_evaldiff", "edge", "spread"])
+def test_integer_evaluation_matches_oracle(oracle_lib, shim, L, name):
+    """The integer evaluation path (bounds, fixed-point frame, reverse-mode
+    sweep, conversion; the device kernel runs this code per lane) against the
+    oracle at the evaluation tolerance, relative to the sum of term moduli."""
+    from parity import TOL, rel_err
+    shim.mpi_eval.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int] + [ctypes.c_void_p] * 3 + \
+        [ctypes.c_int64] + [ctypes.c_void_p] * 3
+    if name == "edge":
+        nv = 12
+        exps = np.zeros((5, nv), np.int8)
+        exps[1, :] = 1
+        exps[2, 3] = 9
+        exps[3, [0, 5, 11]] = [2, 3, 1]
+        exps[4, 7] = 1
+        coef = np.array([[0.5, -0.25], [1.0, 0.0], [-0.3, 0.7], [0.2, 0.2], [0.0, 1.0]])
+        s = synth.System(nv, 2, np.array([3, 2], np.int32), exps, coef)
+        x = synth.unit_points(8, nv, 6, L)
+        rng = synth.SplitMix64(4)
+        x *= 2.0 ** rng.integers(-20, 20, nv * 6).reshape(nv, 1, 1, 6).astype(np.float64)
+        x[2, :, :, 5] = 0.0
+    elif name == "spread":  # points over 60 binades
+        s = synth.config_system("c4_stress_qd")
+        x = synth.unit_points(91 + L, s.n_vars, 8, L)
+        rng = synth.SplitMix64(12)
+        x *= 2.0 ** rng.integers(-30, 30, s.n_vars * 8).reshape(s.n_vars, 1, 1, 8).astype(np.float64)
+    else:
+        s = synth.config_system(name)
+        x = synth.unit_points(55 + L, s.n_vars, 2 if name == "c1_evaldiff" else 5, L)
+    n = x.shape[-1]
+    nt = np.ascontiguousarray(s.n_terms, np.int32)
+    ex = np.ascontiguousarray(s.exps, np.int8)
+    cf = np.ascontiguousarray(s.coef_limbs(L))
+    val = np.empty((s.n_polys, 2, L, n))
+    jac = np.empty((s.n_polys, s.n_vars, 2, L, n))
+    assert shim.mpi_eval(L, s.n_vars, s.n_polys, _p(nt), _p(ex), _p(cf), n, _p(np.ascontiguousarray(x)), _p(val),
+                         _p(jac)) == 0
+    ov, oj = oracle_lib.eval_(s, x)
+    mv, mj = oracle_lib.eval_magnitude(s, x)
+    ev, ej = rel_err(val, ov, mv), rel_err(jac, oj, mj)
+    assert ev <= TOL[L] and ej <= TOL[L], (ev, ej)
+
+
+def _unit(L):
+    """Relative precision of a floating limb string: the L-double target or
+    the 29 (W - 1) + 1 bits the W limbs guarantee, whichever is coarser."""
+    W = {1: 3, 2: 5, 4: 8}[L]
+    return 2.0 ** -min(53 * L, 29 * (W - 1) + 1)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_general_sums_against_oracle(oracle_lib, shim, L):
+    """sum_j e_j z_j with signed small e_j (the adds and subtracts of MGS),
+    error relative to sum_j |e_j| |z_j|, including exact cancellation."""
+    shim.mpi_sum.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                             ctypes.c_void_p]
+    n, k = 200, 5
+    z = _complex(300 + L, n * k, L, spread=10).reshape(n, k, 2, L)
+    z[:, 1] = z[:, 0]  # e = (1, -1, ...): exact cancellation of the first two
+    e = np.array([1, -1, 2, -3, 1], dtype=np.int32)
+    out = np.empty((n, 2, L))
+    assert shim.mpi_sum(L, n, k, _p(np.ascontiguousarray(z)), _p(e), _p(out)) == 0
+    add = lambda u, v: oracle_lib.real_op("add", u, v)
+    mul = lambda u, v: oracle_lib.real_op("mul", u, v)
+    ref = np.zeros((n, 2, L))
+    absum = np.zeros(n)
+    for j in range(k):
+        ee = np.zeros((n, L))
+        ee[:, 0] = e[j]
+        ref[:, 0] = add(ref[:, 0], mul(z[:, j, 0], ee))
+        ref[:, 1] = add(ref[:, 1], mul(z[:, j, 1], ee))
+        absum += abs(e[j]) * np.hypot(z[:, j, 0, 0], z[:, j, 1, 0])
+    err = _cerr(oracle_lib, out, ref)
+    assert np.all(err <= _unit(L) * 64 * absum), np.max(err / absum)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_inverse_square_root_against_oracle(oracle_lib, shim, L):
+    shim.mpi_invsqrt.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    rng = synth.SplitMix64(500 + L)
+    lead = rng.uniform(300) * 2.0 ** rng.integers(-40, 40, 300).astype(np.float64) + 1e-3
+    v = np.ascontiguousarray(synth.random_tails(rng, lead, L).T)
+    out = np.empty_like(v)
+    assert shim.mpi_invsqrt(L, v.shape[0], _p(v), _p(out)) == 0
+    ref = oracle_lib.real_op("div", np.tile(np.eye(1, L), (v.shape[0], 1)), oracle_lib.real_op("sqrt", v))
+    d = oracle_lib.value_diff(out, ref)
+    assert np.all(np.abs(d) <= _unit(L) * 32 * np.abs(ref[:, 0])), np.max(np.abs(d) / np.abs(ref[:, 0]))
