@@ -94,7 +94,9 @@ def _args():
     p.add_argument("--track", default="c0_plain_d,c2_batched_dd",
                    help="tracking workloads to time as well (comma list, '' for none)")
     p.add_argument("--learned", type=int, default=65536,
-                   help="paths of the held-out n = 16 system for learned vs plain (0: skip)")
+                   help="paths of the held-out n = 16 double system for learned vs plain (0: skip)")
+    p.add_argument("--stress", type=int, default=59049,
+                   help="paths of the held-out n = 10 quad double system for learned vs plain (0: skip)")
     return p.parse_args()
 
 
@@ -231,46 +233,77 @@ def _agreement(A, B, tol=1e-10):
     return min(fr)
 
 
-def learned_vs_plain(ht, torch, world, m, n_train=6, train_paths=256, eval_seed=3500):
-    """The learned step against the plain rule on a held-out n = 16 system:
-    the network is trained first (outside the timing) on step-start records
-    of seeded training systems, then both trackers run all m paths."""
+# learned+batched against plain batched: the workload, its tracking and check
+# precisions, the training systems (same shape, other seeds; traces and
+# probes in double) and the held-out system tracked by both arms
+LEARNED_CASES = {
+    "c3_learned_d": dict(limbs=1, check_limbs=2, eval_seed=3500, train_seeds=range(3000, 3006), warm_paths=None),
+    "c4_stress_qd": dict(limbs=4, check_limbs=0, eval_seed=4000, train_seeds=range(4100, 4106), warm_paths=1024),
+}
+
+
+def learned_vs_plain(ht, torch, world, name, m, train_paths=256):
+    """The learned step against the plain rule on a held-out system of the
+    workload's shape: the network is trained first (outside the timing) on
+    step-start records of seeded training systems, then both trackers run all
+    m paths (plus, for the double workload, the double double check of every
+    endpoint) with identical seeds."""
     from paper_1505_00383_gb300 import learned
-    cfg = synth.CONFIGS["c3_learned_d"]
-    prm = ht.ht_default_params(1, h_min=1e-6)
+    case = LEARNED_CASES[name]
+    L, CL = case["limbs"], case["check_limbs"]
+    prm_train = ht.ht_default_params(1, h_min=1e-9)
+    prm = ht.ht_default_params(L, h_min=1e-9)
     t0 = time.perf_counter()
     feats, labs = [], []
-    for seed in range(cfg["train_seeds"][0], cfg["train_seeds"][0] + n_train):
-        s = synth.config_system("c3_learned_d", seed)
+    for seed in case["train_seeds"]:
+        s = synth.config_system(name, seed)
         g = synth.random_gamma(seed)
-        rec = learned.collect_records(s, 1, g, train_paths, prm, stride=2)
-        labs.append(learned.step_labels(s, 1, g, prm, rec))
-        feats.append(learned.features(s, 1, prm, rec))
+        rec = learned.collect_records(s, 1, g, train_paths, prm_train, stride=2)
+        labs.append(learned.step_labels(s, 1, g, prm_train, rec))
+        feats.append(learned.features(s, 1, prm_train, rec))
     net, losses = learned.train(torch.cat(feats), torch.cat(labs), epochs=30, batch=2048, lr=2e-3)
     train_s = time.perf_counter() - t0
-    s = synth.config_system("c3_learned_d", eval_seed)
-    g = synth.random_gamma(eval_seed)
+    s = synth.config_system(name, case["eval_seed"])
+    g = synth.random_gamma(case["eval_seed"])
     out = {}
-    for name, nn in (("plain", None), ("learned", net)):
-        learned.track(s, 1, g, m, prm, net=nn)  # warm-up: workspace, graphs
+    for arm, nn in (("plain", None), ("learned", net)):
+        learned.track(s, L, g, case["warm_paths"] or m, prm, net=nn, check_limbs=CL)  # warm-up: workspace, graphs
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        r = learned.track(s, 1, g, m, prm, net=nn)
+        r = learned.track(s, L, g, m, prm, net=nn, check_limbs=CL)
         sec = time.perf_counter() - t1
-        out[name] = (r, sec)
+        out[arm] = (r, sec)
     (ra, sa), (rb, sb) = out["plain"], out["learned"]
-    from_c = lambda r: ((r["x_end"][:, 0, 0, :] + 1j * r["x_end"][:, 1, 0, :]).T)[r["status"] == 1]
-    agree = _agreement(from_c(ra), from_c(rb))
+
+    def ends(r, checked):  # converged endpoints, leading two limbs
+        X = r["x_check"] if checked else r["x_end"]
+        z = X[:, 0, 0, :] + 1j * X[:, 1, 0, :]
+        if X.shape[2] > 1:
+            z = z + (X[:, 0, 1, :] + 1j * X[:, 1, 1, :])
+        ok = r["status"] == 1
+        if checked:
+            ok = ok & (r["status_check"] == 1)
+        return z.T[ok]
+    chk = CL > L
+    agree = _agreement(ends(ra, chk), ends(rb, chk))
     counts = lambda r: {k: r["stats"][k] for k in ("converged", "failed", "diverged")}
-    return {"paths": m, "precision": "D", "n": 16, "heldout_seed": eval_seed,
-            "plain_s": sa, "learned_s": sb, "plain_paths_per_s": world * m / sa,
-            "learned_paths_per_s": world * m / sb, "speedup": sa / sb,
-            "newton_per_path": {"plain": ra["stats"]["newton"] / m, "learned": rb["stats"]["newton"] / m},
-            "rejects_per_path": {"plain": ra["stats"]["rejects"] / m, "learned": rb["stats"]["rejects"] / m},
-            "counts": {"plain": counts(ra), "learned": counts(rb)},
-            "counts_equal": counts(ra) == counts(rb), "endpoint_agreement_1e-10": agree,
-            "train": {"systems": n_train, "paths_each": train_paths, "samples": int(sum(f.shape[0] for f in feats)),
-                      "first_loss": float(losses[0]), "last_loss": float(losses[-1]), "seconds": train_s}}
+    res = {"paths": m, "precision": NAMES[L], "n": s.n_vars, "heldout_seed": case["eval_seed"],
+           "plain_s": sa, "learned_s": sb, "plain_paths_per_s": world * m / sa,
+           "learned_paths_per_s": world * m / sb, "speedup": sa / sb,
+           "newton_per_path": {"plain": ra["stats"]["newton"] / m, "learned": rb["stats"]["newton"] / m},
+           "rejects_per_path": {"plain": ra["stats"]["rejects"] / m, "learned": rb["stats"]["rejects"] / m},
+           "counts": {"plain": counts(ra), "learned": counts(rb)},
+           "counts_equal": counts(ra) == counts(rb), "endpoint_agreement_1e-10": agree,
+           "train": {"systems": len(case["train_seeds"]), "paths_each": train_paths, "precision": "D",
+                     "samples": int(sum(f.shape[0] for f in feats)), "first_loss": float(losses[0]),
+                     "last_loss": float(losses[-1]), "seconds": train_s}}
+    if chk:
+        checked = lambda r: {"agree_with_tracker_1e-10": _agreement(ends(r, True), ends(r, False)),
+                             "max_last_dx": float(np.max(r["dx_check"][r["status"] == 1]))
+                             if np.any(r["status"] == 1) else None}
+        res["check"] = {"precision": NAMES[CL], "plain": checked(ra), "learned": checked(rb),
+                        "what": "Newton on f from every converged endpoint (timed with the arm)"}
+    return res
 
 
 def run_reference(a):
@@ -427,7 +460,9 @@ def run_ours(a):
     for name in [w for w in a.track.split(",") if w]:
         tracking[name] = track_workload(ht, torch, name, rank, world)
     if a.learned > 0:
-        tracking["c3_learned_vs_plain"] = learned_vs_plain(ht, torch, world, a.learned)
+        tracking["c3_learned_vs_plain"] = learned_vs_plain(ht, torch, world, "c3_learned_d", a.learned)
+    if a.stress > 0:
+        tracking["c4_learned_vs_plain"] = learned_vs_plain(ht, torch, world, "c4_stress_qd", a.stress)
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

@@ -124,6 +124,10 @@ int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, doubl
  * results are bitwise identical; variant 2 meets the same accuracy bound
  * (a small multiple of 2^(-53 L) times the sum of the moduli of the terms of
  * each output) with its own rounding.
+ * The choice also applies to the evaluations inside ht_track_paths for DD and
+ * QD systems: by default (and with variant 2) the tracker evaluates f on the
+ * integer pipe, with variant 0 or 1 on the FP64 pipe.  Double systems always
+ * track with FP64 evaluation.
  */
 int ht_set_eval_config(ht_system* sys, int variant, int threads);
 
@@ -298,6 +302,23 @@ int ht_track_paths(ht_system* f, const int32_t* start_deg, const double* gamma, 
  *   learned step shrinks as usual and the next fallback_steps steps of that
  *   path use the plain rule.
  *
+ *   Start points of another precision.  x0_limbs (1, 2 or 4, at most the
+ *   system's L; 0 means L) is the number of limbs per component of x0, laid
+ *   out [n][2][x0_limbs][n_paths]; the missing limbs are zero.  With fewer
+ *   limbs than L, x0 must not overlap x_end.
+ *
+ *   Endpoint refinement.  With polish_only != 0 (x0 required, no
+ *   init_records, polish_max >= 1) every path starts at t = 1 in the polish
+ *   phase: Newton's method on the target system f alone, in the system's
+ *   precision, until |dx|_inf <= tol_polish max(1, |x|_inf) or polish_max
+ *   rounds; status 1 if the final point is finite, -1 otherwise.  Used to
+ *   check endpoints of a lower-precision run in a higher precision.
+ *
+ *   Last norms.  last_dx_out / last_res_out (device [n_paths], optional)
+ *   receive |dx|_inf and |h|_inf of each path's last Newton round (of its
+ *   last step, or of its last polish round); newton_out (device [n_paths],
+ *   optional) the number of Newton rounds each path took.
+ *
  * Record layout: 16 header doubles [path index in this call, t, h, number of
  * history points nh, |dx|_inf and |h|_inf of the last Newton round, rounds of
  * the last step, last step rejected (0/1), 8 zeros], then the t of the
@@ -313,6 +334,11 @@ typedef struct ht_track_io {
   int32_t fallback_steps;
   const ht_mlp* mlp;
   double rho_min, rho_max;
+  int32_t x0_limbs;      /* limbs per component in x0 (0: the system's L) */
+  int32_t polish_only;   /* nonzero: Newton at t = 1 from x0 only */
+  double* last_dx_out;   /* device [n_paths] or NULL */
+  double* last_res_out;  /* device [n_paths] or NULL */
+  int32_t* newton_out;   /* device [n_paths] or NULL */
 } ht_track_io;
 
 int ht_track_paths_ex(ht_system* f, const int32_t* start_deg, const double* gamma, int64_t n_paths,
@@ -323,9 +349,10 @@ int ht_track_paths_ex(ht_system* f, const int32_t* start_deg, const double* gamm
  * ht_step_labels -- training labels for the learned step: every record is
  * restarted once per multiplier mu_j (mults host [n_mult], n_mult <= 64) with
  * its step h scaled by mu_j, and takes one step of at most newton_max
- * evaluate-correct rounds (p's other settings apply; h_min is lifted).  The
- * label is rho = log of the largest mu_j whose step was accepted (log of the
- * smallest mu_j if none was), and 0 for the second output.
+ * evaluate-correct rounds (p's other settings apply; h_min is lifted).  Among
+ * the accepted probes the label takes the one with the most progress per
+ * round, mu_j / rounds_j (ties to the larger mu_j): rho = log mu_j (log of the
+ * smallest mu_j if no probe was accepted), and 0 for the second output.
  *   records device [n_rec][R]; labels device [n_rec][2] floats.  Blocks.
  */
 int ht_step_labels(ht_system* f, const int32_t* start_deg, const double* gamma, const ht_params* p, int64_t n_rec,

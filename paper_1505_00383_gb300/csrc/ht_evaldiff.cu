@@ -24,7 +24,7 @@
 // array (it stays in L2 while the unit runs), so no scratch memory is used.
 #include "ht_eval.cuh"
 #include "ht_internal.h"
-#include "ht_mpi_eval.cuh"
+#include "ht_int_row.cuh"
 
 namespace ht {
 
@@ -80,51 +80,10 @@ static int launch_v(const EvalArgs& a, int threads, cudaStream_t st) {
 //   3. accumulates value and Jacobian row as fixed-point limbs: the row lives
 //      in place in the output (2L doubles hold exactly 2 x 2L int32 limbs);
 //   4. converts the accumulators to L doubles.
-using mpi::IntW;
-constexpr int kIntMaxVars = 64;
-
-template <int L>
-__device__ __forceinline__ void ld_fix(const double* jrow, int64_t i, int64_t n, int64_t p, int32_t* r, int32_t* im) {
-  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(jrow) + (i * 2) * L * n + p;
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    const unsigned long long a = q[t * n], b = q[(L + t) * n];
-    r[2 * t] = (int32_t)(uint32_t)a;
-    r[2 * t + 1] = (int32_t)(uint32_t)(a >> 32);
-    im[2 * t] = (int32_t)(uint32_t)b;
-    im[2 * t + 1] = (int32_t)(uint32_t)(b >> 32);
-  }
-}
-template <int L>
-__device__ __forceinline__ void st_fix(double* jrow, int64_t i, int64_t n, int64_t p, const int32_t* r,
-                                       const int32_t* im) {
-  unsigned long long* q = reinterpret_cast<unsigned long long*>(jrow) + (i * 2) * L * n + p;
-#pragma unroll
-  for (int t = 0; t < L; ++t) {
-    q[t * n] = (unsigned long long)(uint32_t)r[2 * t] | ((unsigned long long)(uint32_t)r[2 * t + 1] << 32);
-    q[(L + t) * n] = (unsigned long long)(uint32_t)im[2 * t] | ((unsigned long long)(uint32_t)im[2 * t + 1] << 32);
-  }
-}
-
-// The Jacobian row of the unit accumulates in place in the output slots.
-template <int L>
-struct RowAcc {
-  double* jrow;
-  int64_t n, p;
-  __device__ __noinline__ void add(int v, const mpi::fz<IntW<L>::W>& d, int e, int F) {
-    constexpr int WA = IntW<L>::WA;
-    int32_t ar[WA], ai[WA];
-    ld_fix<L>(jrow, v, n, p, ar, ai);
-    mpi::acc_add_fast<IntW<L>::W, WA>(ar, ai, d, e, F);
-    st_fix<L>(jrow, v, n, p, ar, ai);
-  }
-};
-
 template <int L>
 __global__ void __launch_bounds__(128) evaldiff_int_kernel(EvalArgs a, const mpi::fz<IntW<L>::W>* __restrict__ cfz,
                                                            const float* __restrict__ clg) {
-  constexpr int W = IntW<L>::W, WA = IntW<L>::WA;
-  using Z = mpi::fz<W>;
+  using Z = mpi::fz<IntW<L>::W>;
   Z X[kIntMaxVars];
   float lg[kIntMaxVars];
   Z P[64];
@@ -137,43 +96,14 @@ __global__ void __launch_bounds__(128) evaldiff_int_kernel(EvalArgs a, const mpi
     const int j = (int)(u % a.np);
     const int64_t p = (u / a.np) * 32 + lane;
     if (p >= n) continue;
-    double* jrow = a.jac + (int64_t)j * plane;
-    for (int i = 0; i < a.nv; ++i) {
-      double re[L], im[L];
+    int_point<L>(a.v.x, a.nv, n, p, X, lg);
+    double vre[L], vim[L];
+    int_row<L>(a.v.mon_off, a.v.pairs, cfz, clg, a.poly_off[j], a.poly_off[j + 1], X, lg, a.nv,
+               a.jac + (int64_t)j * plane, n, p, vre, vim, P);
 #pragma unroll
-      for (int l = 0; l < L; ++l) {
-        re[l] = a.v.x[((int64_t)(i * 2) * L + l) * n + p];
-        im[l] = a.v.x[((int64_t)(i * 2 + 1) * L + l) * n + p];
-      }
-      X[i] = mpi::from_doubles<W, L>(re, im);
-      lg[i] = mpi::log2_mod(re[0], im[0]);
-    }
-    const int m0 = a.poly_off[j], m1 = a.poly_off[j + 1];
-    int Fv[kIntMaxVars];
-    const int F = mpi::frames_for_poly<WA>(a.v.mon_off, a.v.pairs, clg, m0, m1, lg, a.nv, Fv);
-    int32_t vr[WA], vi[WA];
-#pragma unroll
-    for (int k = 0; k < WA; ++k) vr[k] = vi[k] = 0;
-    for (int i = 0; i < a.nv; ++i) st_fix<L>(jrow, i, n, p, vr, vi);
-    RowAcc<L> acc{jrow, n, p};
-    mpi::eval_poly_int<L>(a.v.mon_off, a.v.pairs, cfz, m0, m1, X, F, Fv, acc, vr, vi, P);
-    // fixed point -> L doubles, value and row in place
-    double o[L];
-    mpi::fixed_to_doubles<WA, L>(vr, F, o);
-#pragma unroll
-    for (int l = 0; l < L; ++l) a.val[((int64_t)(j * 2) * L + l) * n + p] = o[l];
-    mpi::fixed_to_doubles<WA, L>(vi, F, o);
-#pragma unroll
-    for (int l = 0; l < L; ++l) a.val[((int64_t)(j * 2 + 1) * L + l) * n + p] = o[l];
-    for (int i = 0; i < a.nv; ++i) {
-      int32_t ar[WA], ai[WA];
-      ld_fix<L>(jrow, i, n, p, ar, ai);
-      mpi::fixed_to_doubles<WA, L>(ar, Fv[i], o);
-#pragma unroll
-      for (int l = 0; l < L; ++l) jrow[((int64_t)(i * 2) * L + l) * n + p] = o[l];
-      mpi::fixed_to_doubles<WA, L>(ai, Fv[i], o);
-#pragma unroll
-      for (int l = 0; l < L; ++l) jrow[((int64_t)(i * 2 + 1) * L + l) * n + p] = o[l];
+    for (int l = 0; l < L; ++l) {
+      a.val[((int64_t)(j * 2) * L + l) * n + p] = vre[l];
+      a.val[((int64_t)(j * 2 + 1) * L + l) * n + p] = vim[l];
     }
   }
 }

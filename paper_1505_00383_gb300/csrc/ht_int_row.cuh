@@ -1,0 +1,103 @@
+// One polynomial's value and gradient row on the integer pipe, for one point
+// per lane (device only): the per-output frames, the reverse-mode sweep of
+// ht_mpi_eval.cuh with the row's fixed-point accumulators in place in the
+// caller's output row, and the conversion of every output to L doubles.  The
+// evaluation kernel and the tracker both call it.
+#pragma once
+#include "ht_mpi_eval.cuh"
+
+namespace ht {
+
+using mpi::IntW;
+constexpr int kIntMaxVars = 64;
+
+// The fixed-point accumulators of entry i of a row in the vertical layout
+// [i][2][L][n] (path/point index p fastest): 2L doubles hold 2 x 2L int32.
+template <int L>
+__device__ __forceinline__ void ld_fix(const double* jrow, int64_t i, int64_t n, int64_t p, int32_t* r, int32_t* im) {
+  const unsigned long long* q = reinterpret_cast<const unsigned long long*>(jrow) + (i * 2) * L * n + p;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    const unsigned long long a = q[t * n], b = q[(L + t) * n];
+    r[2 * t] = (int32_t)(uint32_t)a;
+    r[2 * t + 1] = (int32_t)(uint32_t)(a >> 32);
+    im[2 * t] = (int32_t)(uint32_t)b;
+    im[2 * t + 1] = (int32_t)(uint32_t)(b >> 32);
+  }
+}
+template <int L>
+__device__ __forceinline__ void st_fix(double* jrow, int64_t i, int64_t n, int64_t p, const int32_t* r,
+                                       const int32_t* im) {
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(jrow) + (i * 2) * L * n + p;
+#pragma unroll
+  for (int t = 0; t < L; ++t) {
+    q[t * n] = (unsigned long long)(uint32_t)r[2 * t] | ((unsigned long long)(uint32_t)r[2 * t + 1] << 32);
+    q[(L + t) * n] = (unsigned long long)(uint32_t)im[2 * t] | ((unsigned long long)(uint32_t)im[2 * t + 1] << 32);
+  }
+}
+
+// The Jacobian row accumulates in place in the output slots.
+template <int L>
+struct RowAcc {
+  double* jrow;
+  int64_t n, p;
+  __device__ __noinline__ void add(int v, const mpi::fz<IntW<L>::W>& d, int e, int F) {
+    constexpr int WA = IntW<L>::WA;
+    int32_t ar[WA], ai[WA];
+    ld_fix<L>(jrow, v, n, p, ar, ai);
+    mpi::acc_add_fast<IntW<L>::W, WA>(ar, ai, d, e, F);
+    st_fix<L>(jrow, v, n, p, ar, ai);
+  }
+};
+
+// The lane's point converted once: X[i] (limb string) and lg[i] = log2 |x_i|,
+// from x in the layout [nv][2][L][n].
+template <int L>
+__device__ __forceinline__ void int_point(const double* __restrict__ x, int nv, int64_t n, int64_t p,
+                                          mpi::fz<IntW<L>::W>* X, float* lg) {
+  for (int i = 0; i < nv; ++i) {
+    double re[L], im[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+      re[l] = x[((int64_t)(i * 2) * L + l) * n + p];
+      im[l] = x[((int64_t)(i * 2 + 1) * L + l) * n + p];
+    }
+    X[i] = mpi::from_doubles<IntW<L>::W, L>(re, im);
+    lg[i] = mpi::log2_mod(re[0], im[0]);
+  }
+}
+
+// Monomials m0..m1 of one polynomial at the lane's point: the value as L
+// doubles per component (vre, vim) and the gradient written as doubles into
+// jrow ([nv][2][L][n], entry i at point p).  P is scratch for the forward
+// products (max monomial size entries).
+template <int L>
+__device__ void int_row(const int32_t* __restrict__ mon_off, const uint16_t* __restrict__ pairs,
+                        const mpi::fz<IntW<L>::W>* __restrict__ cfz, const float* __restrict__ clg, int m0, int m1,
+                        const mpi::fz<IntW<L>::W>* X, const float* lg, int nv, double* jrow, int64_t n, int64_t p,
+                        double* vre, double* vim, mpi::fz<IntW<L>::W>* P) {
+  constexpr int WA = IntW<L>::WA;
+  int Fv[kIntMaxVars];
+  const int F = mpi::frames_for_poly<WA>(mon_off, pairs, clg, m0, m1, lg, nv, Fv);
+  int32_t vr[WA], vi[WA];
+#pragma unroll
+  for (int k = 0; k < WA; ++k) vr[k] = vi[k] = 0;
+  for (int i = 0; i < nv; ++i) st_fix<L>(jrow, i, n, p, vr, vi);
+  RowAcc<L> acc{jrow, n, p};
+  mpi::eval_poly_int<L>(mon_off, pairs, cfz, m0, m1, X, F, Fv, acc, vr, vi, P);
+  mpi::fixed_to_doubles<WA, L>(vr, F, vre);
+  mpi::fixed_to_doubles<WA, L>(vi, F, vim);
+  double o[L];
+  for (int i = 0; i < nv; ++i) {
+    int32_t ar[WA], ai[WA];
+    ld_fix<L>(jrow, i, n, p, ar, ai);
+    mpi::fixed_to_doubles<WA, L>(ar, Fv[i], o);
+#pragma unroll
+    for (int l = 0; l < L; ++l) jrow[((int64_t)(i * 2) * L + l) * n + p] = o[l];
+    mpi::fixed_to_doubles<WA, L>(ai, Fv[i], o);
+#pragma unroll
+    for (int l = 0; l < L; ++l) jrow[((int64_t)(i * 2 + 1) * L + l) * n + p] = o[l];
+  }
+}
+
+}  // namespace ht

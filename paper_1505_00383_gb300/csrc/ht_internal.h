@@ -13,7 +13,7 @@ struct ht_system {
   int nv = 0, np = 0, limbs = 0, device = 0;
   int64_t M = 0, n_pairs = 0;
   int max_k = 0, max_exp = 0, max_deg = 0;
-  int eval_variant = -1;         // 0 unrolled bodies, 1 compact bodies, -1 default (compact)
+  int eval_variant = -1;         // 0 unrolled, 1 compact FP64 bodies, 2 integer limbs, -1 default
   int eval_threads = 0;          // CTA size of the evaluation kernel, 0 = default (128)
   std::vector<int32_t> n_terms;  // host copies
   std::vector<int8_t> exps;

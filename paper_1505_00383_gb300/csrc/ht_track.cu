@@ -22,6 +22,7 @@
 // ([entry][2][L][m], path index fastest) -- the "work space for multiple
 // paths" of Table tabmemory.
 #include "ht_eval.cuh"
+#include "ht_int_row.cuh"
 #include "ht_internal.h"
 #include "ht_mlp.cuh"
 #include "ht_track.h"
@@ -157,9 +158,16 @@ __global__ void init_kernel(TrackArgs a) {
       a.last_its[p] = (int8_t)r[6];
       a.last_rej[p] = (int8_t)r[7];
     } else {
+      if (a.x0) {  // the caller's start points, x0_limbs limbs each (missing limbs zero)
+        for (int i = 0; i < a.n; ++i)
+          for (int c = 0; c < 2; ++c)
+            for (int l = 0; l < L; ++l)
+              a.x[(((int64_t)i * 2 + c) * L + l) * a.m + p] =
+                  l < a.x0_limbs ? a.x0[(((int64_t)i * 2 + c) * a.x0_limbs + l) * a.m + p] : 0.0;
+      }
       for (int i = 0; i < a.n; ++i) st<L>(a.hx, i, a.m, p, ld<L>(a.x, i, a.m, p));
-      a.ht[p] = 0.0;
-      a.t[p] = 0.0;
+      a.ht[p] = a.polish_only ? 1.0 : 0.0;
+      a.t[p] = a.polish_only ? 1.0 : 0.0;
       a.h[p] = a.prm.h0;
       a.nh[p] = 1;
       a.last_dx[p] = 0.0;
@@ -170,11 +178,12 @@ __global__ void init_kernel(TrackArgs a) {
     a.t1[p] = 0.0;
     a.status[p] = 0;
     a.it[p] = 0;
-    a.phase[p] = PH_TRACK;
+    a.phase[p] = (a.polish_only && !a.init_rec) ? PH_POLISH : PH_TRACK;
     a.fallback[p] = 0;
     a.steps[p] = 0;
     a.rejects[p] = 0;
     a.newton[p] = 0;
+    if (a.newton_out) a.newton_out[p] = 0;
     a.idx0[p] = (int32_t)p;
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.count0 = (int32_t)a.m;
@@ -245,19 +254,55 @@ __global__ void __launch_bounds__(32) mgs_kernel(double* A, double* R, double* x
   mgs_team<L>(A, R, x, rows, cols, n_sys, p, p < n_sys, 0, 1);
 }
 
+// The learned proposal for the paths of one warp (all 32 lanes call it; want
+// marks the lanes whose path starts a learned step): features, the network
+// on the tensor cores, and h e^rho clamped.  Out of line so that the
+// network's registers do not weigh on the Newton rounds' allocation.
+template <int L>
+__device__ __noinline__ double learned_step(const TrackArgs& a, MlpWarpSmem& stage, bool want, int64_t p, double t,
+                                            double h, int nh, int cap) {
+  float f[FEAT];
+  if (want)
+    step_features<L>(f, t, h, nh, cap, a.n, a.ht + p, a.m, a.hx + p, a.m, a.last_dx[p], a.last_res[p],
+                     (int)a.last_its[p], (int)a.last_rej[p], a.prm.newton_max);
+  else
+    for (int i = 0; i < FEAT; ++i) f[i] = 0.0f;
+  float y[2];
+  mlp_forward_warp(*static_cast<const MlpSmem*>(a.mlp_img), stage, f, y);
+  double hs = h;
+  if (want) {
+    const double rho = fmin(a.rho_max, fmax(a.rho_min, (double)y[0]));
+    hs = fmin(a.prm.h_max, fmax(a.prm.h_min, h * exp(rho)));
+  }
+  return hs;
+}
+
 // One Newton step (plus the bookkeeping around it) for `iters` rounds.
 // LEARN: at every step start warp 0 evaluates the step-size network for its 32
 // paths on the tensor cores and scales the step (see ht_track_paths_ex).
-template <int L, bool LEARN>
-__global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
+template <int L>
+__device__ __forceinline__ cx<L> cx_from(const double* re, const double* im) {
+  if constexpr (L == 1) {
+    return cx<1>{re[0], im[0]};
+  } else if constexpr (L == 2) {
+    return cx<2>{dd{re[0], re[1]}, dd{im[0], im[1]}};
+  } else {
+    return cx<4>{qd{{re[0], re[1], re[2], re[3]}}, qd{{im[0], im[1], im[2], im[3]}}};
+  }
+}
+
+// INT: f and its Jacobian rows on the integer pipe (int_row: exact sums in
+// per-output fixed-point frames), the rest of the round in FP64 arithmetic.
+template <int L, bool LEARN, bool INT>
+__global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kernel(TrackArgs a) {
   __shared__ double red[4][8][32];  // per-warp partials: residual, update, point norms; finiteness
   __shared__ double sh_h[32];       // learned step of each lane's path
   __shared__ long long sh_slot[32]; // trace record slot of each lane's path (-1: none)
-  extern __shared__ __align__(16) unsigned char dsm[];  // network image when LEARN
-  if constexpr (LEARN) {
-    mlp_load(*reinterpret_cast<MlpSmem*>(dsm), a.mlp_wbf, a.mlp_master);
-    __syncthreads();
-  }
+  // The network's weights are read from the device image (L1/L2): staging
+  // them in shared memory would enlarge the shared-memory carveout and take
+  // L1 capacity from the Newton workspace.  Only warp 0's sample staging
+  // lives in shared memory.
+  __shared__ MlpWarpSmem mlp_stage;
   const int cap = a.prm.max_order + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, T = blockDim.x >> 5;
   const int n = a.n, W = n + 1;
@@ -323,23 +368,10 @@ __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
         }
       }
       if constexpr (LEARN) {
-        if (warp == 0) {
-          float f[FEAT];
-          if (start && fb == 0)
-            step_features<L>(f, t, h, nh, cap, n, a.ht + p, m, a.hx + p, m, a.last_dx[p], a.last_res[p],
-                             (int)a.last_its[p], (int)a.last_rej[p], a.prm.newton_max);
-          else
-            for (int i = 0; i < FEAT; ++i) f[i] = 0.0f;
-          float y[2];
-          mlp_forward_warp(*reinterpret_cast<const MlpSmem*>(dsm),
-                           *reinterpret_cast<MlpWarpSmem*>(dsm + sizeof(MlpSmem)), f, y);
-          double hs = h;
-          if (start && fb == 0) {
-            const double rho = fmin(a.rho_max, fmax(a.rho_min, (double)y[0]));
-            hs = fmin(a.prm.h_max, fmax(a.prm.h_min, h * exp(rho)));
-          }
-          sh_h[lane] = hs;
-        }
+        // warp 0 runs the network only in rounds where one of its paths
+        // starts a learned step (about one round in three)
+        if (warp == 0 && __any_sync(0xffffffffu, start && fb == 0))
+          sh_h[lane] = learned_step<L>(a, mlp_stage, start && fb == 0, p, t, h, nh, cap);
         __syncthreads();
         if (start && fb == 0) {
           h = sh_h[lane];
@@ -379,9 +411,21 @@ __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
       double pres = 0.0;
       if (act) {
         cx<L> gs = cscale_r(gamma, r_diff<L>(1.0, tt));
+        using Z = mpi::fz<IntW<L>::W>;
+        Z X[INT ? kIntMaxVars : 1], P[INT ? kIntMaxVars : 1];
+        float lg[INT ? kIntMaxVars : 1];
+        if constexpr (INT) int_point<L>(a.xp, n, m, p, X, lg);
         for (int j = warp; j < n; j += T) {
           double* Arow = a.A + (int64_t)j * rowA;
-          cx<L> fj = eval_poly<L>(v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), n, p, Arow);
+          cx<L> fj;
+          if constexpr (INT) {
+            double vre[L], vim[L];
+            int_row<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
+                       __ldg(a.poly_off + j + 1), X, lg, n, Arow, m, p, vre, vim, P);
+            fj = cx_from<L>(vre, vim);
+          } else {
+            fj = eval_poly<L>(v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), n, p, Arow);
+          }
           for (int i = 0; i < n; ++i) st<L>(Arow, i, m, p, cscale(ld<L>(Arow, i, m, p), tt));
           const int d = __ldg(a.deg + j);
           cx<L> xj = ld<L>(a.xp, j, m, p);
@@ -535,12 +579,16 @@ __global__ void __launch_bounds__(256) track_kernel(TrackArgs a) {
         a.steps[p] = steps;
         a.rejects[p] = rejects;
         a.newton[p] = newton;
+        if (a.newton_out) a.newton_out[p] = newton;
         a.fallback[p] = (int8_t)fb;
         if (step_end) {
           a.last_dx[p] = ndx;
           a.last_res[p] = nres;
           a.last_its[p] = (int8_t)last_its_v;
           a.last_rej[p] = (int8_t)last_rej_v;
+        } else if (ph == PH_POLISH) {  // norms of the latest polish round
+          a.last_dx[p] = ndx;
+          a.last_res[p] = nres;
         }
       }
       __syncthreads();
@@ -608,6 +656,17 @@ int launch_mgs_l(double* A, double* R, double* x, int rows, int cols, int64_t n_
 }
 
 #if HT_LIMBS == 1
+__global__ void __launch_bounds__(256) mlp_image_kernel(MlpSmem* img, const __nv_bfloat16* __restrict__ wbf,
+                                                        const float* __restrict__ master) {
+  mlp_load(*img, wbf, master);
+}
+size_t mlp_image_bytes() { return sizeof(MlpSmem); }
+int launch_mlp_image(void* img, const __nv_bfloat16* wbf, const float* master, cudaStream_t st) {
+  mlp_image_kernel<<<1, 256, 0, st>>>(static_cast<MlpSmem*>(img), wbf, master);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "mlp image launch");
+}
+
 int launch_compact(const int32_t* idx_in, const int32_t* count_in, const int8_t* status, int32_t* idx_out,
                    int32_t* count_out, cudaStream_t st) {
   compact_kernel<<<1, 1024, 0, st>>>(idx_in, count_in, status, idx_out, count_out);
@@ -628,23 +687,21 @@ int launch_init_l(const TrackArgs& a, cudaStream_t st) {
 
 template <int L>
 int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_t st) {
-  const bool learn = a.mlp_wbf != nullptr;
-  const size_t dsm = learn ? sizeof(MlpSmem) + sizeof(MlpWarpSmem) : 0;
-  int per_sm = 0;
-  if (learn) {
-    cudaFuncSetAttribute(track_kernel<L, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L, true>, 32 * team, dsm);
-  } else {
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L, false>, 32 * team, 0);
-  }
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)sm_count() * per_sm;
-  if (grid > max_groups) grid = max_groups;
-  if (grid < 1) grid = 1;
+  const bool learn = a.mlp_img != nullptr;
+  const bool in = L > 1 && a.int_eval;  // the double tracker keeps FP64 evaluation
+  auto go = [&](auto kern) {
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * team, 0);
+    if (per_sm < 1) per_sm = 1;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    if (grid > max_groups) grid = max_groups;
+    if (grid < 1) grid = 1;
+    kern<<<(unsigned)grid, 32 * team, 0, st>>>(a);
+  };
   if (learn)
-    track_kernel<L, true><<<(unsigned)grid, 32 * team, dsm, st>>>(a);
+    in ? go(track_kernel<L, true, L != 1>) : go(track_kernel<L, true, false>);
   else
-    track_kernel<L, false><<<(unsigned)grid, 32 * team, 0, st>>>(a);
+    in ? go(track_kernel<L, false, L != 1>) : go(track_kernel<L, false, false>);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HT_OK : cuda_fail(e, "track launch");
 }
@@ -662,7 +719,7 @@ int launch_features_l(const double* rec, int64_t n_rec, int n, int cap, int newt
 template <int L>
 int track_occupancy_l(int team) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L, false>, 32 * team, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, track_kernel<L, false, false>, 32 * team, 0);
   return per_sm;
 }
 

@@ -31,6 +31,9 @@ struct TrackArgs {
   const int32_t* mon_off;
   const uint16_t* pairs;
   const double* coef;
+  const void* cfz;     // coefficients in the integer format (mpi::fz<W>), for int_eval
+  const float* clg;    // log2 |c|
+  int int_eval;        // DD/QD: evaluate f on the integer pipe
   const int32_t* deg;  // start system degrees [n]
   double gamma_re, gamma_im;
   int n;
@@ -54,6 +57,10 @@ struct TrackArgs {
   int32_t* steps;
   int32_t* rejects;
   int32_t* newton;
+  int32_t* newton_out;     // per-path Newton rounds ([m]) or nullptr
+  const double* x0;        // caller's start points ([n][2][x0_limbs][m]) or nullptr
+  int x0_limbs;
+  int polish_only;         // start every path at t = 1 in the polish phase
   const int32_t* idx_in;   // active path indices of this launch
   const int32_t* count_in; // their number (device)
   int32_t* idx0;           // init: identity index list
@@ -70,8 +77,7 @@ struct TrackArgs {
   unsigned long long* trace_count;
   int64_t trace_cap;
   int trace_stride;
-  const __nv_bfloat16* mlp_wbf;  // nullptr: plain rule
-  const float* mlp_master;
+  const void* mlp_img;     // network image (MlpSmem layout, device memory); nullptr: plain rule
   int fallback_steps;
   double rho_min, rho_max;
 };
@@ -88,6 +94,8 @@ template <int L>
 int track_occupancy_l(int team);
 template <int L>
 int launch_features_l(const double* rec, int64_t n_rec, int n, int cap, int newton_max, float* feat, cudaStream_t st);
+int launch_mlp_image(void* img, const __nv_bfloat16* wbf, const float* master, cudaStream_t st);
+size_t mlp_image_bytes();
 int launch_compact(const int32_t* idx_in, const int32_t* count_in, const int8_t* status, int32_t* idx_out,
                    int32_t* count_out, cudaStream_t st);
 

@@ -64,17 +64,26 @@ __global__ void probe_records_kernel(const double* __restrict__ rec, int64_t n_r
   }
 }
 
-// Label of record r: rho = log of the largest multiplier whose single probe
-// step was accepted (t moved past the record's t), else log of the smallest.
+// Label of record r: among the multipliers whose single probe step was
+// accepted (t moved past the record's t), the one with the most progress per
+// Newton round, mu_j / rounds_j (ties to the larger mu_j); rho = its log, or
+// the log of the smallest multiplier if no probe was accepted.
 __global__ void labels_kernel(const double* __restrict__ rec, int64_t n_rec, int64_t R, int n_mult,
                               const double* __restrict__ mults, const double* __restrict__ t_end,
-                              float* __restrict__ labels) {
+                              const int32_t* __restrict__ rounds, float* __restrict__ labels) {
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rec; r += (int64_t)gridDim.x * blockDim.x) {
     const double t0 = rec[r * R + 1];
-    double best = -1.0, lo = mults[0];
+    double best = -1.0, best_eff = -1.0, lo = mults[0];
     for (int j = 0; j < n_mult; ++j) {
       lo = fmin(lo, mults[j]);
-      if (t_end[r * n_mult + j] > t0) best = fmax(best, mults[j]);
+      if (t_end[r * n_mult + j] > t0) {
+        const int k = rounds[r * n_mult + j];
+        const double eff = mults[j] / (double)(k > 0 ? k : 1);
+        if (eff > best_eff || (eff == best_eff && mults[j] > best)) {
+          best_eff = eff;
+          best = mults[j];
+        }
+      }
     }
     labels[r * 2 + 0] = (float)log(best > 0.0 ? best : lo);
     labels[r * 2 + 1] = 0.0f;
@@ -210,6 +219,14 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
     return set_error(HT_EINVAL, "ht_track_paths_ex: init_records must be device memory");
   if (IO.mlp && (IO.fallback_steps < 0 || IO.fallback_steps > 100 || !(IO.rho_max >= IO.rho_min)))
     return set_error(HT_EINVAL, "ht_track_paths_ex: invalid learned-step settings");
+  const int x0_limbs = IO.x0_limbs > 0 ? IO.x0_limbs : L;
+  if (IO.x0_limbs < 0 || x0_limbs > L || (x0_limbs == 3))
+    return set_error(HT_EINVAL, "ht_track_paths_ex: x0_limbs=%d (1, 2 or 4, at most the system's %d)", IO.x0_limbs, L);
+  if (IO.polish_only && (!x0 || IO.init_records || P.polish_max < 1))
+    return set_error(HT_EINVAL, "ht_track_paths_ex: polish_only needs x0, no init_records and polish_max >= 1");
+  if ((IO.last_dx_out && !is_device_ptr(IO.last_dx_out)) || (IO.last_res_out && !is_device_ptr(IO.last_res_out)) ||
+      (IO.newton_out && !is_device_ptr(IO.newton_out)))
+    return set_error(HT_EINVAL, "ht_track_paths_ex: last_dx_out, last_res_out and newton_out must be device memory");
   if (stats) std::memset(stats, 0, sizeof *stats);
   if (n_paths == 0) return HT_OK;
   if (!x_end || !status || !t_end || !is_device_ptr(x_end) || !is_device_ptr(status) || !is_device_ptr(t_end) ||
@@ -231,7 +248,8 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
          o_h = take(m * 8), o_t1 = take(m * 8), o_it = take(m), o_ph = take(m), o_nh = take(m),
          o_steps = take(m * 4), o_rej = take(m * 4), o_newt = take(m * 4), o_idx0 = take((m + 1) * 4),
          o_idx1 = take((m + 1) * 4), o_cnt = take(2 * 4), o_deg = take(n * 4), o_ldx = take(m * 8),
-         o_lres = take(m * 8), o_lits = take(m), o_lrej = take(m), o_fb = take(m);
+         o_lres = take(m * 8), o_lits = take(m), o_lrej = take(m), o_fb = take(m),
+         o_img = IO.mlp ? take(mlp_image_bytes()) : 0;
   int rc = ensure_track_ws(s, off, st);
   if (rc != HT_OK) return rc;
   char* w = (char*)s->d_track_ws;
@@ -240,6 +258,11 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.mon_off = s->d_mon_off;
   a.pairs = s->d_pairs;
   a.coef = s->d_coef;
+  a.cfz = s->d_coef_fz;
+  a.clg = s->d_coef_lg;
+  // DD and QD evaluate f on the integer pipe unless an FP64 evaluation variant
+  // was chosen for this system (ht_set_eval_config 0 or 1)
+  a.int_eval = L > 1 && s->d_coef_fz && n <= 64 && s->max_k <= 64 && (s->eval_variant == -1 || s->eval_variant == 2);
   a.deg = (const int32_t*)(w + o_deg);
   a.gamma_re = gamma[0];
   a.gamma_im = gamma[1];
@@ -278,36 +301,50 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.trace_count = (unsigned long long*)IO.trace_count;
   a.trace_cap = IO.trace_capacity;
   a.trace_stride = IO.trace_stride > 0 ? IO.trace_stride : 1;
-  a.mlp_wbf = IO.mlp ? mlp_bf16(IO.mlp) : nullptr;
-  a.mlp_master = IO.mlp ? mlp_master(IO.mlp) : nullptr;
+  a.mlp_img = IO.mlp ? (const void*)(w + o_img) : nullptr;
+  a.newton_out = IO.newton_out;
   a.fallback_steps = IO.fallback_steps;
   a.rho_min = IO.rho_min;
   a.rho_max = IO.rho_max;
+  a.x0 = IO.init_records ? nullptr : x0;
+  a.x0_limbs = x0_limbs;
+  a.polish_only = IO.polish_only ? 1 : 0;
+  if (a.x0 && x0_limbs != L) {  // the widening copy in init_kernel must not read what it writes
+    const char *b0 = (const char*)x0, *e0 = b0 + (size_t)n * 2 * x0_limbs * m * sizeof(double);
+    const char *b1 = (const char*)x_end, *e1 = b1 + n * cxb;
+    if (b0 < e1 && b1 < e0) return set_error(HT_EINVAL, "ht_track_paths_ex: x0 with fewer limbs overlaps x_end");
+  }
   cudaError_t e = cudaMemcpyAsync((void*)a.deg, start_deg, n * sizeof(int32_t), cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: upload degrees");
   if (IO.init_records) {
     // the init kernel takes every path's state from its record
   } else if (x0) {
-    e = cudaMemcpyAsync(x_end, x0, n * cxb, cudaMemcpyDeviceToDevice, st);
-    if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: copy x0");
+    // the init kernel copies (and widens) x0 into x_end
   } else {
     rc = by_limbs(L, [&](auto c) { return launch_start_l<decltype(c)::value>(n, a.deg, first_path, m, x_end, st); });
     if (rc != HT_OK) return rc;
   }
   rc = by_limbs(L, [&](auto c) { return launch_init_l<decltype(c)::value>(a, st); });
   if (rc != HT_OK) return rc;
+  if (IO.mlp) {
+    rc = launch_mlp_image(w + o_img, mlp_bf16(IO.mlp), mlp_master(IO.mlp), st);
+    if (rc != HT_OK) return rc;
+  }
 
   // Rounds: [track (iters Newton steps) ; compact] x rounds_per_sync per host
   // read of the active count, captured once per team size as a CUDA graph.
   const int iters = P.iters_per_launch > 0 ? P.iters_per_launch : 4;
   const int rounds = P.rounds_per_sync > 0 ? P.rounds_per_sync : 8;
-  const int sms = sm_count();
+  // Team size: the largest power of two up to 8 warps and n.  More warps per
+  // group means fewer groups in flight for the same FP64 issue rate, so the
+  // per-path workspace (A and R, 2 n (n + 1) complex entries per path) of the
+  // resident groups stays in L2; on the n = 16 double workload 8 warps beat 1
+  // warp by 1.7x and 4 warps by 4 %.
   auto pick_team = [&](int64_t active) {
+    (void)active;
     if (P.team_warps > 0) return P.team_warps;
-    int64_t groups = (active + 31) / 32;
-    int64_t target = (int64_t)sms * 8;  // two warps per SM sub-partition
     int t = 1;
-    while (t < 8 && t < n && groups * t * 2 <= target) t *= 2;
+    while (t < 8 && 2 * t <= n) t *= 2;
     return t;
   };
   int64_t active = m;
@@ -367,6 +404,10 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
     loops += (int64_t)rounds * iters;
     if (loops > max_loops && active > 0) return set_error(HT_ETIMEOUT, "ht_track_paths: paths still active after %lld Newton rounds", (long long)loops);
   }
+  if (IO.last_dx_out) e = cudaMemcpyAsync(IO.last_dx_out, a.last_dx, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e == cudaSuccess && IO.last_res_out)
+    e = cudaMemcpyAsync(IO.last_res_out, a.last_res, m * sizeof(double), cudaMemcpyDeviceToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_track_paths: last norms");
   if (stats) {
     std::vector<int8_t> hs(m);
     std::vector<int32_t> hst(m), hrj(m), hnw(m);
@@ -417,9 +458,10 @@ int ht_step_labels(ht_system* s, const int32_t* start_deg, const double* gamma, 
   const int64_t R = rec_size(n, L, prm->max_order + 1), P = n_rec * n_mult;
   if (P > 0x7fffffff) return set_error(HT_EINVAL, "ht_step_labels: too many probes");
   cudaStream_t st = (cudaStream_t)stream;
-  size_t b_rec = (size_t)P * R * 8, b_x = (size_t)n * 2 * L * P * 8, b_t = (size_t)P * 8, b_m = 64 * 8;
+  size_t b_rec = (size_t)P * R * 8, b_x = (size_t)n * 2 * L * P * 8, b_t = (size_t)P * 8, b_m = 64 * 8,
+         b_k = ((size_t)P * 4 + 255) / 256 * 256;
   char* buf = nullptr;
-  cudaError_t e = cudaMalloc((void**)&buf, b_rec + b_x + b_t + (size_t)P + b_m + 1024);
+  cudaError_t e = cudaMalloc((void**)&buf, b_rec + b_x + b_t + b_k + (size_t)P + b_m + 1024);
   if (e != cudaSuccess) {
     cudaGetLastError();
     return set_error(HT_ENOMEM, "ht_step_labels: probe workspace");
@@ -428,7 +470,8 @@ int ht_step_labels(ht_system* s, const int32_t* start_deg, const double* gamma, 
   double* px = (double*)(buf + b_rec);
   double* pt = (double*)(buf + b_rec + b_x);
   double* pm = (double*)(buf + b_rec + b_x + b_t);
-  int8_t* pst = (int8_t*)(buf + b_rec + b_x + b_t + b_m);
+  int32_t* pk = (int32_t*)(buf + b_rec + b_x + b_t + b_m);
+  int8_t* pst = (int8_t*)(buf + b_rec + b_x + b_t + b_m + b_k);
   int rc = HT_OK;
   e = cudaMemcpyAsync(pm, mults, n_mult * 8, cudaMemcpyHostToDevice, st);
   if (e != cudaSuccess) rc = cuda_fail(e, "ht_step_labels");
@@ -442,10 +485,11 @@ int ht_step_labels(ht_system* s, const int32_t* start_deg, const double* gamma, 
     ht_track_io io;
     std::memset(&io, 0, sizeof io);
     io.init_records = prec;
+    io.newton_out = pk;
     rc = ht_track_paths_ex(s, start_deg, gamma, P, 0, nullptr, &pp, px, pst, pt, nullptr, nullptr, &io, stream);
   }
   if (rc == HT_OK) {
-    labels_kernel<<<256, 256, 0, st>>>(records, n_rec, R, n_mult, pm, pt, labels);
+    labels_kernel<<<256, 256, 0, st>>>(records, n_rec, R, n_mult, pm, pt, pk, labels);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "ht_step_labels");
   }

@@ -66,7 +66,9 @@ class ht_params(ctypes.Structure):
 class ht_track_io(ctypes.Structure):
     _fields_ = [("init_records", ctypes.c_void_p), ("trace", ctypes.c_void_p), ("trace_capacity", ctypes.c_int64),
                 ("trace_count", ctypes.c_void_p), ("trace_stride", ctypes.c_int32), ("fallback_steps", ctypes.c_int32),
-                ("mlp", ctypes.c_void_p), ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double)]
+                ("mlp", ctypes.c_void_p), ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double),
+                ("x0_limbs", ctypes.c_int32), ("polish_only", ctypes.c_int32), ("last_dx_out", ctypes.c_void_p),
+                ("last_res_out", ctypes.c_void_p), ("newton_out", ctypes.c_void_p)]
 
 
 class ht_stats(ctypes.Structure):

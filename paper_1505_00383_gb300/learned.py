@@ -7,9 +7,9 @@ keeps the device buffers (torch tensors):
    every ``stride``-th step start (``ht_track_paths_ex`` with a trace buffer);
 2. ``step_labels``: each record is restarted with its step scaled by each
    multiplier in ``MULTS`` for one step with the tracker's own limit of
-   evaluate-correct rounds; the label is the log of the largest multiplier that
-   was accepted (``ht_step_labels``) -- the step the state allowed, not the
-   plain rule's;
+   evaluate-correct rounds; the label is the log of the accepted multiplier
+   with the most progress per Newton round (``ht_step_labels``) -- the step the
+   state allowed at the least cost, not the plain rule's;
 3. ``features`` (``ht_step_features``) and ``train`` (``ht_mlp_train``: BF16
    tensor-core forward, FP32 backward, Adam);
 4. ``track(..., net=...)`` runs the tracker with the network proposing steps.
@@ -106,9 +106,13 @@ def train(feat, lab, epochs=30, batch=4096, lr=2e-3, seed=1):
     return net, losses
 
 
-def track(system, limbs, gamma, n_paths, params, net=None, fallback_steps=1, first_path=0):
+def track(system, limbs, gamma, n_paths, params, net=None, fallback_steps=1, first_path=0, check_limbs=0,
+          check_params=None):
     """ht_track_paths_ex with (net given) or without the learned step; returns
-    host arrays and stats."""
+    host arrays and stats.  With check_limbs > limbs the endpoints are then
+    checked in that precision: Newton's method on the target system from
+    every endpoint (polish_only), giving x_check, status_check and the last
+    update norms dx_check."""
     torch = _torch()
     n = system.n_vars
     hs = ht.system_from(system, limbs)
@@ -120,5 +124,17 @@ def track(system, limbs, gamma, n_paths, params, net=None, fallback_steps=1, fir
     if net is not None:
         io = ht.ht_track_io(mlp=net.handle, fallback_steps=fallback_steps, rho_min=RHO_RANGE[0], rho_max=RHO_RANGE[1])
     ht.ht_track_paths_ex(hs, system.degrees(), gamma, n_paths, first_path, None, params, x, st, t, None, stats, io)
+    out = dict(stats=stats.as_dict())
+    if check_limbs > limbs:
+        hc = ht.system_from(system, check_limbs)
+        pc = check_params or ht.ht_default_params(check_limbs)
+        xc = torch.empty((n, 2, check_limbs, n_paths), dtype=torch.float64, device="cuda")
+        sc = torch.empty_like(st)
+        tc = torch.empty_like(t)
+        dxc = torch.empty((n_paths,), dtype=torch.float64, device="cuda")
+        ioc = ht.ht_track_io(x0_limbs=limbs, polish_only=1, last_dx_out=dxc.data_ptr())
+        ht.ht_track_paths_ex(hc, system.degrees(), gamma, n_paths, 0, x, pc, xc, sc, tc, None, None, ioc)
+        out.update(x_check=xc.cpu().numpy(), status_check=sc.cpu().numpy(), dx_check=dxc.cpu().numpy())
     torch.cuda.synchronize()
-    return dict(x_end=x.cpu().numpy(), status=st.cpu().numpy(), t_end=t.cpu().numpy(), stats=stats.as_dict())
+    out.update(x_end=x.cpu().numpy(), status=st.cpu().numpy(), t_end=t.cpu().numpy())
+    return out

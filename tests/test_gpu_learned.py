@@ -161,14 +161,55 @@ def test_features_follow_their_definition(ht):
         assert np.all(f[k, 9:] == 0)
 
 
+def test_labels_follow_their_definition(ht):
+    """Each record is probed once per multiplier (one step, the tracker's
+    round limit); the label is the log of the accepted multiplier with the
+    most progress per Newton round, ties to the larger; the smallest if none
+    was accepted.  Probes re-run here one multiplier at a time."""
+    from paper_1505_00383_gb300 import learned
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    prm = ht.ht_default_params(1, h_min=1e-6)
+    rec = learned.collect_records(s, 1, gam, 32, prm, stride=3)
+    rec = rec[::5].contiguous()
+    lab = learned.step_labels(s, 1, gam, prm, rec).cpu().numpy()
+    R = rec.shape[1]
+    n_rec = rec.shape[0]
+    t0 = rec[:, 1].cpu().numpy()
+    acc = np.zeros((n_rec, len(learned.MULTS)), bool)
+    rounds = np.zeros((n_rec, len(learned.MULTS)), np.int64)
+    hs = ht.system_from(s, 1)
+    pp = ht.ht_default_params(1, h_min=1e-300, max_steps=1, polish_max=0)
+    for j, mu in enumerate(learned.MULTS):
+        r = rec.clone()
+        r[:, 2] *= mu
+        x = torch.empty((s.n_vars, 2, 1, n_rec), dtype=torch.float64, device="cuda")
+        st = torch.empty((n_rec,), dtype=torch.int8, device="cuda")
+        t = torch.empty((n_rec,), dtype=torch.float64, device="cuda")
+        k = torch.empty((n_rec,), dtype=torch.int32, device="cuda")
+        io = ht.ht_track_io(init_records=r.data_ptr(), newton_out=k.data_ptr())
+        ht.ht_track_paths_ex(hs, s.degrees(), gam, n_rec, 0, None, pp, x, st, t, None, None, io)
+        torch.cuda.synchronize()
+        acc[:, j] = t.cpu().numpy() > t0
+        rounds[:, j] = k.cpu().numpy()
+    assert acc.any() and (~acc).any() and np.all(rounds >= 1) and np.all(rounds <= prm.newton_max)
+    for q in range(n_rec):
+        best, eff = None, -1.0
+        for j, mu in enumerate(learned.MULTS):
+            if acc[q, j] and (mu / rounds[q, j] > eff or (mu / rounds[q, j] == eff and mu > best)):
+                best, eff = mu, mu / rounds[q, j]
+        want = np.float32(np.log(best if best is not None else min(learned.MULTS)))
+        assert lab[q, 0] == want and lab[q, 1] == 0.0, (q, lab[q], want, acc[q], rounds[q])
+
+
 def test_trained_network_gains_over_the_plain_rule(ht):
-    """Train on step-start records of training systems (labels: the largest
-    step each state allowed), then track held-out systems: the learned step
+    """Train on step-start records of training systems (labels: the step
+    each state allowed at the least cost per round), then track held-out systems: the learned step
     needs fewer Newton rounds than the plain rule, with the same endpoint set
     and the same counts of converged, failed and diverged paths."""
     from paper_1505_00383_gb300 import learned
     cfg = synth.CONFIGS["c3_learned_d"]
-    prm = ht.ht_default_params(1, h_min=1e-6)
+    prm = ht.ht_default_params(1, h_min=1e-9)
     feats, labs = [], []
     for seed in range(cfg["train_seeds"][0], cfg["train_seeds"][0] + 6):
         s = synth.config_system("c3_learned_d", seed)

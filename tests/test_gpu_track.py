@@ -101,10 +101,12 @@ def _gpu_params(ht, L, **over):
     return ht.ht_default_params(L, **over)
 
 
-def track_gpu(ht, system, L, m, first=0, start_deg=None, gamma=(0.6, 0.8), **over):
+def track_gpu(ht, system, L, m, first=0, start_deg=None, gamma=(0.6, 0.8), eval_variant=None, **over):
     n = system.n_vars
     deg = system.degrees() if start_deg is None else np.asarray(start_deg, np.int32)
     hs = ht.system_from(system, L)
+    if eval_variant is not None:
+        ht.ht_set_eval_config(hs, eval_variant, 0)
     x = torch.full((n, 2, L, m), np.nan, dtype=torch.float64, device="cuda")
     status = torch.full((m,), 9, dtype=torch.int8, device="cuda")
     t = torch.full((m,), np.nan, dtype=torch.float64, device="cuda")
@@ -184,6 +186,19 @@ def test_team_size_and_launch_shape_do_not_change_results(ht):
             assert np.array_equal(r[k], base[k], equal_nan=True), (tw, it, rs, k)
 
 
+@pytest.mark.parametrize("L", [2, 4])
+def test_team_size_does_not_change_integer_evaluation_results(ht, L):
+    """With f on the integer pipe each lane's arithmetic is the same for any
+    split of polynomials and MGS columns over the team's warps."""
+    s = synth.config_system("c4_stress_qd" if L == 4 else "c2_batched_dd")
+    gam = synth.random_gamma(1)
+    base = track_gpu(ht, s, L, 96, gamma=gam, team_warps=1, iters_per_launch=2, rounds_per_sync=2)
+    for tw in (2, 8):
+        r = track_gpu(ht, s, L, 96, gamma=gam, team_warps=tw)
+        for k in ("x_end", "status", "t_end", "steps"):
+            assert np.array_equal(r[k], base[k], equal_nan=True), (tw, k)
+
+
 def test_sharded_path_ranges_union_equals_full_run(ht):
     """Paths are independent (Section 1): tracking path ranges separately (as
     separate GPUs would) gives the full run's results."""
@@ -197,14 +212,17 @@ def test_sharded_path_ranges_union_equals_full_run(ht):
     assert np.array_equal(x, full["x_end"]) and np.array_equal(st, full["status"])
 
 
-@pytest.mark.parametrize("name,L,m,sample", [("c2_batched_dd", 2, 4096, 48), ("c4_stress_qd", 4, 1024, 16)])
-def test_batched_tracker_sampled_paths_match_oracle(ht, name, L, m, sample):
+@pytest.mark.parametrize("name,L,m,sample,ev", [("c2_batched_dd", 2, 4096, 48, None), ("c2_batched_dd", 2, 4096, 24, 1),
+                                              ("c4_stress_qd", 4, 1024, 16, None), ("c4_stress_qd", 4, 512, 8, 1)])
+def test_batched_tracker_sampled_paths_match_oracle(ht, name, L, m, sample, ev):
     """The batched tracker on the workload shape (all 4,096 DD paths; 1,024 of
-    the QD paths); a seeded sample of paths is re-tracked one by one by the
-    oracle and must end with the same status and endpoint."""
+    the QD paths), with f evaluated on the integer pipe (the default for DD
+    and QD) or on the FP64 pipe (ev = 1); a seeded sample of paths is
+    re-tracked one by one by the oracle and must end with the same status and
+    endpoint."""
     s = synth.config_system(name)
     gam = synth.random_gamma(synth.CONFIGS[name]["seed"])
-    g = track_gpu(ht, s, L, m, gamma=gam, h_min=1e-6)
+    g = track_gpu(ht, s, L, m, gamma=gam, h_min=1e-6, eval_variant=ev)
     assert set(np.unique(g["status"])) <= {1, -1, -2}
     assert g["stats"]["converged"] + g["stats"]["failed"] + g["stats"]["diverged"] == m
     rng = synth.SplitMix64(7)
@@ -234,3 +252,78 @@ def test_tracker_rejects_bad_arguments(ht):
         rect = synth.System(6, 5, s.n_terms[:5], s.exps[:40], s.coef[:40])
         ht.ht_track_paths(ht.system_from(rect, 1), [2] * 6, (1.0, 0.0), 4, 0, None, None, x, st, t)
     ht.ht_track_paths(hs, [2] * 6, (1.0, 0.0), 0, 0, None, None, x, st, t)  # no paths: no-op
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_endpoint_check_in_higher_precision_matches_oracle(ht, L):
+    """Complex double tracking, then Newton on f alone in DD / QD from the
+    double endpoints (polish_only, x0 with one limb): every path gives the
+    oracle's own DD / QD endpoint of that path to working precision, and the
+    last update is at the precision's level."""
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    m = 64
+    g = track_gpu(ht, s, 1, m, gamma=gam, h_min=1e-9)
+    conv = g["status"] == 1
+    hs = ht.system_from(s, L)
+    x0 = dev(g["x_end"])
+    x = torch.full((s.n_vars, 2, L, m), np.nan, dtype=torch.float64, device="cuda")
+    st = torch.full((m,), 9, dtype=torch.int8, device="cuda")
+    t = torch.zeros((m,), dtype=torch.float64, device="cuda")
+    ldx = torch.full((m,), np.nan, dtype=torch.float64, device="cuda")
+    io = ht.ht_track_io(x0_limbs=1, polish_only=1, last_dx_out=ldx.data_ptr())
+    ht.ht_track_paths_ex(hs, s.degrees(), gam, m, 0, x0, ht.ht_default_params(L, polish_max=6), x, st, t, None,
+                         None, io)
+    torch.cuda.synchronize()
+    xc, sc, dxc = x.cpu().numpy(), st.cpu().numpy(), ldx.cpu().numpy()
+    assert np.all(sc[conv] == 1) and np.all(t.cpu().numpy() == 1.0)
+    assert np.max(dxc[conv]) <= {2: 1e-24, 4: 1e-48}[L]
+    o = track_oracle(s, L, np.arange(m), gamma=gam, h_min=1e-9)
+    # paths that reach the same root in the double run and the oracle's run
+    both = conv & (o["status"] == 1)
+    d = np.max(np.abs(to_complex(g["x_end"]) - to_complex(o["x_end"])), axis=1)
+    same = both & (d <= 1e-8)
+    assert same.sum() >= both.sum() - 2 and same.sum() > 0
+    e = cerr(xc[..., same], o["x_end"][..., same])
+    assert np.max(e) <= {2: 1e-26, 4: 1e-50}[L], np.max(e)
+
+
+def test_narrow_start_points_are_widened(ht):
+    """x0 given in one limb for a DD system: the missing limbs are zero, so
+    the start solutions of x_i^2 - 1 (exactly +-1) give the same paths as the
+    system's own start solutions."""
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    m = 64
+    a = track_gpu(ht, s, 2, m, gamma=gam, h_min=1e-9)
+    x0 = torch.empty((s.n_vars, 2, 1, m), dtype=torch.float64, device="cuda")
+    ht.ht_start_solutions(s.n_vars, s.degrees(), 1, 0, m, x0)
+    hs = ht.system_from(s, 2)
+    x = torch.full((s.n_vars, 2, 2, m), np.nan, dtype=torch.float64, device="cuda")
+    st = torch.full((m,), 9, dtype=torch.int8, device="cuda")
+    t = torch.zeros((m,), dtype=torch.float64, device="cuda")
+    ht.ht_track_paths_ex(hs, s.degrees(), gam, m, 0, x0, ht.ht_default_params(2, h_min=1e-9), x, st, t, None, None,
+                         ht.ht_track_io(x0_limbs=1))
+    torch.cuda.synchronize()
+    assert np.array_equal(st.cpu().numpy(), a["status"])
+    assert np.array_equal(x.cpu().numpy(), a["x_end"], equal_nan=True)
+
+
+def test_endpoint_check_rejects_bad_arguments(ht):
+    s = synth.config_system("c0_plain_d")
+    hs = ht.system_from(s, 2)
+    m = 4
+    x = torch.zeros((6, 2, 2, m), dtype=torch.float64, device="cuda")
+    x1 = torch.zeros((6, 2, 1, m), dtype=torch.float64, device="cuda")
+    st = torch.zeros((m,), dtype=torch.int8, device="cuda")
+    t = torch.zeros((m,), dtype=torch.float64, device="cuda")
+    p = ht.ht_default_params(2)
+    with pytest.raises(ht.HTError):  # polish_only without start points
+        ht.ht_track_paths_ex(hs, [2] * 6, (1.0, 0.0), m, 0, None, p, x, st, t, None, None, ht.ht_track_io(polish_only=1))
+    with pytest.raises(ht.HTError):  # more limbs than the system
+        ht.ht_track_paths_ex(hs, [2] * 6, (1.0, 0.0), m, 0, x1, p, x, st, t, None, None, ht.ht_track_io(x0_limbs=4))
+    with pytest.raises(ht.HTError):  # widening in place
+        ht.ht_track_paths_ex(hs, [2] * 6, (1.0, 0.0), m, 0, x, p, x, st, t, None, None, ht.ht_track_io(x0_limbs=1))
+    with pytest.raises(ht.HTError):  # no polish rounds
+        ht.ht_track_paths_ex(hs, [2] * 6, (1.0, 0.0), m, 0, x1, ht.ht_default_params(2, polish_max=0), x, st, t, None,
+                             None, ht.ht_track_io(polish_only=1, x0_limbs=1))
