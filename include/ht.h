@@ -124,10 +124,11 @@ int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, doubl
  * results are bitwise identical; variant 2 meets the same accuracy bound
  * (a small multiple of 2^(-53 L) times the sum of the moduli of the terms of
  * each output) with its own rounding.
- * The choice also applies to the evaluations inside ht_track_paths for DD and
- * QD systems: by default (and with variant 2) the tracker evaluates f on the
- * integer pipe, with variant 0 or 1 on the FP64 pipe.  Double systems always
- * track with FP64 evaluation.
+ * The choice also applies inside ht_track_paths for DD and QD systems with
+ * n <= 32: by default (and with variant 2) the tracker evaluates f on the
+ * integer pipe, and for QD also solves the Newton systems there
+ * (ht_mgs_solve_ex variant 2); with variant 0 or 1 it uses the FP64 pipe
+ * throughout.  Double systems always track on the FP64 pipe.
  */
 int ht_set_eval_config(ht_system* sys, int variant, int threads);
 
@@ -241,6 +242,21 @@ int ht_start_solutions(int n, const int32_t* degrees, int limbs, int64_t first, 
  * rows >= cols >= 1.  A rank-deficient system gives non-finite x.  Async.
  */
 int ht_mgs_solve(int limbs, int rows, int cols, int64_t n_sys, double* Ab, double* R, double* x, void* stream);
+
+/*
+ * ht_mgs_solve_ex -- ht_mgs_solve with a choice of arithmetic:
+ *   variant 0  error-free DD/QD arithmetic on the FP64 pipe (ht_mgs_solve);
+ *   variant 2  integer limbs (limbs 2 or 4, rows <= 64): every entry is read
+ *              as a radix-2^29 limb string, every dot product and norm is one
+ *              exact fixed-point sum of its products rounded once, 1/r_qq
+ *              comes from Newton's iteration for 1/sqrt; results are written
+ *              back as doubles (the leading 53-bit pieces of each value).
+ * The tracker uses variant 2 for QD systems unless ht_set_eval_config chose
+ * an FP64 variant.  Errors as ht_mgs_solve; HT_EUNSUPPORTED for
+ * variant 2 with limbs 1 or more than 64 rows.
+ */
+int ht_mgs_solve_ex(int limbs, int variant, int rows, int cols, int64_t n_sys, double* Ab, double* R, double* x,
+                    void* stream);
 
 /*
  * ht_compact -- the scan of Table tabjobidx: path_idx receives, in increasing

@@ -43,6 +43,22 @@ struct fz {
   int32_t r[W], i[W];
 };
 
+// Bit length of v (0 for 0): one count-leading-zeros instruction.
+HT_HD int bitlen32(uint32_t v) {
+#if defined(__CUDA_ARCH__)
+  return 32 - __clz((int)v);
+#else
+  return v ? 32 - __builtin_clz(v) : 0;
+#endif
+}
+HT_HD int bitlen64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  return 64 - __clzll((long long)v);
+#else
+  return v ? 64 - __builtin_clzll(v) : 0;
+#endif
+}
+
 HT_HD int64_t dbits(double d) {
   int64_t b;
   std::memcpy(&b, &d, 8);
@@ -158,6 +174,29 @@ HT_HD fz<W> from_doubles(const double* re, const double* im) {
   return z;
 }
 
+// Keep the top limbs below 2^28 in magnitude (the invariant from_doubles
+// sets up): a right shift of both limb strings by 1 or 2 bits when the top
+// limb of either component grew past it.  With both operands' top limbs below
+// 2^28 a product's top limb stays below 2^29, so column sums never overflow
+// and every consumer (products, shifts into fixed-point frames) may treat the
+// top limb as a 29-bit signed value.
+template <int W>
+HT_HD void normalize_top(fz<W>& z) {
+  const int32_t tr = z.r[W - 1] < 0 ? -z.r[W - 1] : z.r[W - 1];
+  const int32_t ti = z.i[W - 1] < 0 ? -z.i[W - 1] : z.i[W - 1];
+  const int32_t t = tr > ti ? tr : ti;
+  const int s = t >= (1 << 29) ? 2 : (t >= (1 << 28) ? 1 : 0);
+  if (s == 0) return;
+#pragma unroll
+  for (int k = 0; k < W - 1; ++k) {
+    z.r[k] = (int32_t)((((uint32_t)z.r[k] >> s) | ((uint32_t)z.r[k + 1] << (RB - s))) & (uint32_t)MASK);
+    z.i[k] = (int32_t)((((uint32_t)z.i[k] >> s) | ((uint32_t)z.i[k + 1] << (RB - s))) & (uint32_t)MASK);
+  }
+  z.r[W - 1] >>= s;
+  z.i[W - 1] >>= s;
+  z.f += s;
+}
+
 // Complex product.  Columns W-2 .. 2W-1 of the exact limb product (the lower
 // ones only feed a carry below the result's last limb and are dropped).
 template <int W>
@@ -206,6 +245,7 @@ HT_HD fz<W> mul(const fz<W>& a, const fz<W>& b) {
     z.r[W - 1] += (int32_t)(tr * (1LL << RB));  // fold a sign-only top column
     z.i[W - 1] += (int32_t)(ti * (1LL << RB));
   }
+  normalize_top<W>(z);
   return z;
 }
 
@@ -325,11 +365,7 @@ HT_HD void fixed_to_doubles(const int32_t* a, int F, double* out) {
 #pragma unroll
   for (int l = 0; l < L; ++l) out[l] = 0.0;
   if (top < 0) return;
-  int tb = 0;
-  {
-    uint64_t v = (uint64_t)m[top];
-    while (v >> (tb + 1)) ++tb;
-  }
+  const int tb = bitlen64((uint64_t)m[top]) - 1;
   int hi_bit = RB * top + tb;  // absolute bit index of the leading bit
 #pragma unroll
   for (int l = 0; l < L; ++l) {

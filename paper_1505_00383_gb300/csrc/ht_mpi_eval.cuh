@@ -73,6 +73,24 @@ HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const f
   return frame_of<WA>(E, cnt);
 }
 
+// The complex product as called from the sweep.  On the device the 5- and
+// 8-limb products (a few hundred instructions each when unrolled) run out of
+// line, one copy for all call sites, so the sweep's code stays within the
+// instruction cache.
+#if defined(__CUDA_ARCH__)
+template <int W>
+__device__ __noinline__ fz<W> mul_ool(const fz<W>& a, const fz<W>& b) {
+  return mul<W>(a, b);
+}
+#endif
+template <int W>
+HT_HD fz<W> mul_sw(const fz<W>& a, const fz<W>& b) {
+#if defined(__CUDA_ARCH__)
+  if constexpr (W >= 5) return mul_ool<W>(a, b);
+#endif
+  return mul<W>(a, b);
+}
+
 // Value (fixed-point vr, vi in frame F) and gradient (through acc.add(var, d,
 // e, Fv[var])) of the monomials m0..m1 at the point X (converted variables);
 // P is scratch for k forward products.
@@ -88,13 +106,13 @@ HT_HD void eval_poly_int(const int32_t* mon_off, const uint16_t* pairs, const fz
     Z cf = cfz[m];
     for (int r = 0; r < k; ++r) {
       const uint16_t q = pr[r];
-      for (int e = 1; e < (q >> 8); ++e) cf = mul<W>(cf, X[q & 0xff]);
+      for (int e = 1; e < (q >> 8); ++e) cf = mul_sw<W>(cf, X[q & 0xff]);
     }
     if (k == 0) {
       acc_add_fast<W, WA>(vr, vi, cf, 1, F);
       continue;
     }
-    for (int r = 0; r < k; ++r) P[r] = mul<W>(r == 0 ? cf : P[r - 1], X[pr[r] & 0xff]);
+    for (int r = 0; r < k; ++r) P[r] = mul_sw<W>(r == 0 ? cf : P[r - 1], X[pr[r] & 0xff]);
     acc_add_fast<W, WA>(vr, vi, P[k - 1], 1, F);
     if (k == 1) {
       acc.add(pr[0] & 0xff, cf, pr[0] >> 8, Fv[pr[0] & 0xff]);
@@ -105,11 +123,11 @@ HT_HD void eval_poly_int(const int32_t* mon_off, const uint16_t* pairs, const fz
     Z S = X[q & 0xff];
     for (int r = k - 2; r >= 1; --r) {
       q = pr[r];
-      acc.add(q & 0xff, mul<W>(P[r - 1], S), q >> 8, Fv[q & 0xff]);
-      S = mul<W>(S, X[q & 0xff]);
+      acc.add(q & 0xff, mul_sw<W>(P[r - 1], S), q >> 8, Fv[q & 0xff]);
+      S = mul_sw<W>(S, X[q & 0xff]);
     }
     q = pr[0];
-    acc.add(q & 0xff, mul<W>(cf, S), q >> 8, Fv[q & 0xff]);
+    acc.add(q & 0xff, mul_sw<W>(cf, S), q >> 8, Fv[q & 0xff]);
   }
 }
 

@@ -15,17 +15,14 @@ namespace mpi {
 // than one unit of it).  Zero gives a very small E.
 template <int W>
 HT_HD int bound_exp(const fz<W>& z) {
-  int b = -1;
-  for (int k = W - 1; k >= 0 && b < 0; --k) {
+  for (int k = W - 1; k >= 0; --k) {
     const int32_t ar = z.r[k] < 0 ? -z.r[k] : z.r[k], ai = z.i[k] < 0 ? -z.i[k] : z.i[k];
     const int32_t mx = ar > ai ? ar : ai;
     if (mx != 0) {
-      int bl = 0;
-      while ((1 << bl) <= mx) ++bl;  // bit length of mx
-      b = z.f + RB * k + bl + 1;     // (mx + 1) * 2^(29 k + f) bounds the lower limbs too
+      return z.f + RB * k + bitlen32((uint32_t)mx) + 1;  // (mx + 1) 2^(29 k + f) bounds the lower limbs too
     }
   }
-  return b < 0 ? -30000 : b;
+  return -30000;
 }
 
 // Fixed-point complex (WA limbs each, frame F) to a floating fz<W>: the W
@@ -64,6 +61,7 @@ HT_HD fz<W> fixed_to_fz(const int32_t* ar_in, const int32_t* ai_in, int F) {
     z.r[W - 1] = (int32_t)r[WA - 1];
     z.i[W - 1] = (int32_t)im[WA - 1];
   }
+  normalize_top<W>(z);
   return z;
 }
 
@@ -87,9 +85,7 @@ HT_HD fz<W> sum(const fz<W>* z, const int* e, int n) {
   for (int k = 0; k < n; ++k) {
     if (e[k] == 0 || is_zero<W>(z[k])) continue;
     const int ek = e[k] < 0 ? -e[k] : e[k];
-    int lb = 0;
-    while ((1 << lb) < ek) ++lb;
-    const int b = bound_exp<W>(z[k]) + lb;
+    const int b = bound_exp<W>(z[k]) + bitlen32((uint32_t)(ek - 1));  // + ceil(log2 |e_k|)
     E = b > E ? b : E;
     fmax = z[k].f > fmax ? z[k].f : fmax;
   }
@@ -101,8 +97,7 @@ HT_HD fz<W> sum(const fz<W>* z, const int* e, int n) {
     for (int k = 0; k < W; ++k) zero.r[k] = zero.i[k] = 0;
     return zero;
   }
-  int head = 1;
-  while ((1 << head) < n + 1) ++head;
+  const int head = bitlen32((uint32_t)n) > 1 ? bitlen32((uint32_t)n) : 1;  // 2^head >= n + 1
   int F = E + head - (RB * (WA - 1) + 28);
   F = F > fmax - (RB - 1) ? F : fmax - (RB - 1);
   for (int k = 0; k < n; ++k)
@@ -164,6 +159,55 @@ HT_HD fz<W> inv_sqrt(const fz<W>& v, int steps) {
     y.f -= 1;  // halve
   }
   return y;
+}
+
+// ------------------------------------------------------------ least squares
+// Building blocks of modified Gram-Schmidt on columns of limb strings (the
+// tracker's corrector, Section 2): every dot product and norm is one exact
+// fixed-point sum of its products, rounded once.
+template <int W>
+HT_HD int inv_sqrt_steps() {
+  return W >= 8 ? 3 : 2;  // from a 53-bit seed: 2 steps give 212 bits, 3 give 424
+}
+// sum_i conj(q_i) a_i over i < rows (rows <= N; scratch holds rows entries)
+template <int W, int N>
+HT_HD fz<W> dot_conj(const fz<W>* q, const fz<W>* a, int rows, fz<W>* scratch) {
+  int e[N];
+  for (int i = 0; i < rows; ++i) {
+    scratch[i] = mul<W>(conj<W>(q[i]), a[i]);
+    e[i] = 1;
+  }
+  return sum<W, N>(scratch, e, rows);
+}
+// sum_i |a_i|^2 (imaginary part exactly zero: the cross columns cancel)
+template <int W, int N>
+HT_HD fz<W> norm2(const fz<W>* a, int rows, fz<W>* scratch) {
+  int e[N];
+  for (int i = 0; i < rows; ++i) {
+    scratch[i] = mul<W>(a[i], conj<W>(a[i]));
+    e[i] = 1;
+  }
+  return sum<W, N>(scratch, e, rows);
+}
+// a_i -= r q_i
+template <int W>
+HT_HD void sub_scaled(fz<W>* a, const fz<W>& r, const fz<W>* q, int rows) {
+  for (int i = 0; i < rows; ++i) a[i] = sub<W>(a[i], mul<W>(r, q[i]));
+}
+// sum_k e_k z_k with e = (1, -1, -1, ...): b - sum_j r_j x_j for the back
+// substitution (terms[0] = b, terms[1..n] = the products)
+template <int W, int N>
+HT_HD fz<W> first_minus_rest(const fz<W>* terms, int n) {
+  int e[N];
+  for (int k = 0; k < n; ++k) e[k] = k == 0 ? 1 : -1;
+  return sum<W, N>(terms, e, n);
+}
+// Limb string to L doubles per component (the fixed-point reading of the
+// limbs: limbs 0..W-2 in [0, 2^29), top signed, frame f).
+template <int W, int L>
+HT_HD void to_doubles(const fz<W>& z, double* re, double* im) {
+  fixed_to_doubles<W, L>(z.r, z.f, re);
+  fixed_to_doubles<W, L>(z.i, z.f, im);
 }
 
 }  // namespace mpi

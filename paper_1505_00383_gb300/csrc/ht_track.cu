@@ -24,6 +24,7 @@
 #include "ht_eval.cuh"
 #include "ht_int_row.cuh"
 #include "ht_internal.h"
+#include "ht_mpi_ops.cuh"
 #include "ht_mlp.cuh"
 #include "ht_track.h"
 
@@ -247,11 +248,84 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
   __syncthreads();
 }
 
-// Standalone batched least squares (one system per lane, one warp per CTA).
+// The same least squares on the integer pipe (DD, QD): entries are read as
+// limb strings (exact conversion of the stored doubles), every dot product
+// and norm is one exact fixed-point sum of its products rounded once, 1/r_qq
+// comes from Newton's iteration for 1/sqrt, and results are stored back as
+// doubles.  The column owner loads and normalises column q; the other warps
+// reload it after the barrier.  Layouts and R's diagonal (1/r_qq) as above.
 template <int L>
+__device__ __forceinline__ mpi::fz<IntW<L>::W> ldz(const double* base, int64_t e, int64_t m, int64_t p) {
+  const double* q = base + (e * 2) * L * m + p;
+  double re[L], im[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    re[l] = q[l * m];
+    im[l] = q[(L + l) * m];
+  }
+  return mpi::from_doubles<IntW<L>::W, L>(re, im);
+}
+template <int L>
+__device__ __forceinline__ void stz(double* base, int64_t e, int64_t m, int64_t p, const mpi::fz<IntW<L>::W>& z) {
+  double* q = base + (e * 2) * L * m + p;
+  double re[L], im[L];
+  mpi::to_doubles<IntW<L>::W, L>(z, re, im);
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    q[l * m] = re[l];
+    q[(L + l) * m] = im[l];
+  }
+}
+
+template <int L, int N>
+__device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
+                             int warp, int T) {
+  constexpr int W = IntW<L>::W;  // rows <= N
+  using Z = mpi::fz<W>;
+  const int Wc = cols + 1;
+  Z Q[N], col[N], S[N + 1];
+  for (int q = 0; q < cols; ++q) {
+    if (warp == q % T && act) {
+      for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc + q, m, p);
+      const Z nrm = mpi::norm2<W, N>(Q, rows, S);
+      const Z inv = mpi::inv_sqrt<W>(nrm, mpi::inv_sqrt_steps<W>());
+      for (int i = 0; i < rows; ++i) stz<L>(A, (int64_t)i * Wc + q, m, p, mpi::mul<W>(Q[i], inv));
+      stz<L>(R, (int64_t)q * Wc + q, m, p, inv);
+    }
+    __syncthreads();
+    const int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
+    if (act && j0 <= cols) {
+      for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc + q, m, p);
+      for (int j = j0; j <= cols; j += T) {
+        for (int i = 0; i < rows; ++i) col[i] = ldz<L>(A, (int64_t)i * Wc + j, m, p);
+        const Z r = mpi::dot_conj<W, N>(Q, col, rows, S);
+        stz<L>(R, (int64_t)q * Wc + j, m, p, r);
+        mpi::sub_scaled<W>(col, r, Q, rows);
+        for (int i = 0; i < rows; ++i) stz<L>(A, (int64_t)i * Wc + j, m, p, col[i]);
+      }
+    }
+    __syncthreads();
+  }
+  if (warp == 0 && act) {  // back substitution, solution in col[]
+    for (int q = cols - 1; q >= 0; --q) {
+      int k = 0;
+      S[k++] = ldz<L>(R, (int64_t)q * Wc + cols, m, p);
+      for (int j = q + 1; j < cols; ++j) S[k++] = mpi::mul<W>(ldz<L>(R, (int64_t)q * Wc + j, m, p), col[j]);
+      col[q] = mpi::mul<W>(mpi::first_minus_rest<W, N + 1>(S, k), ldz<L>(R, (int64_t)q * Wc + q, m, p));
+    }
+    for (int q = 0; q < cols; ++q) stz<L>(x, q, m, p, col[q]);
+  }
+  __syncthreads();
+}
+
+// Standalone batched least squares (one system per lane, one warp per CTA).
+template <int L, bool INT>
 __global__ void __launch_bounds__(32) mgs_kernel(double* A, double* R, double* x, int rows, int cols, int64_t n_sys) {
   int64_t p = (int64_t)blockIdx.x * 32 + threadIdx.x;
-  mgs_team<L>(A, R, x, rows, cols, n_sys, p, p < n_sys, 0, 1);
+  if constexpr (INT)
+    mgs_team_int<L, kIntMaxVars>(A, R, x, rows, cols, n_sys, p, p < n_sys, 0, 1);
+  else
+    mgs_team<L>(A, R, x, rows, cols, n_sys, p, p < n_sys, 0, 1);
 }
 
 // The learned proposal for the paths of one warp (all 32 lanes call it; want
@@ -280,6 +354,10 @@ __device__ __noinline__ double learned_step(const TrackArgs& a, MlpWarpSmem& sta
 // One Newton step (plus the bookkeeping around it) for `iters` rounds.
 // LEARN: at every step start warp 0 evaluates the step-size network for its 32
 // paths on the tensor cores and scales the step (see ht_track_paths_ex).
+// Largest n for which DD/QD tracking runs on the integer pipe (local arrays
+// of the evaluation and of MGS are sized by it).
+constexpr int kIntMaxTrack = 32;
+
 template <int L>
 __device__ __forceinline__ cx<L> cx_from(const double* re, const double* im) {
   if constexpr (L == 1) {
@@ -412,8 +490,8 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
       if (act) {
         cx<L> gs = cscale_r(gamma, r_diff<L>(1.0, tt));
         using Z = mpi::fz<IntW<L>::W>;
-        Z X[INT ? kIntMaxVars : 1], P[INT ? kIntMaxVars : 1];
-        float lg[INT ? kIntMaxVars : 1];
+        Z X[INT ? kIntMaxTrack : 1], P[INT ? kIntMaxTrack : 1];
+        float lg[INT ? kIntMaxTrack : 1];
         if constexpr (INT) int_point<L>(a.xp, n, m, p, X, lg);
         for (int j = warp; j < n; j += T) {
           double* Arow = a.A + (int64_t)j * rowA;
@@ -443,7 +521,13 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
       }
       __syncthreads();
       // ---- C: least squares J dx = -h by modified Gram-Schmidt
-      mgs_team<L>(a.A, a.R, a.dx, n, n, m, p, act, warp, T);
+      // QD solves on the integer pipe; a DD complex product is only 38 FP64
+      // instructions, and there the FP64 MGS was measured faster (1.6 s
+      // against 3.1 s for the whole n = 12, 4,096-path DD run)
+      if constexpr (INT && L == 4)
+        mgs_team_int<L, kIntMaxTrack>(a.A, a.R, a.dx, n, n, m, p, act, warp, T);
+      else
+        mgs_team<L>(a.A, a.R, a.dx, n, n, m, p, act, warp, T);
       // ---- D: x <- x + dx on this warp's coordinates; partial norms
       double pdx = 0.0, pxp = 0.0;
       if (act) {
@@ -648,9 +732,12 @@ int launch_start_l(int n, const int32_t* d_deg, int64_t first, int64_t count, do
 }
 
 template <int L>
-int launch_mgs_l(double* A, double* R, double* x, int rows, int cols, int64_t n_sys, cudaStream_t st) {
+int launch_mgs_l(double* A, double* R, double* x, int rows, int cols, int64_t n_sys, int variant, cudaStream_t st) {
   if (n_sys == 0) return HT_OK;
-  mgs_kernel<L><<<(unsigned)((n_sys + 31) / 32), 32, 0, st>>>(A, R, x, rows, cols, n_sys);
+  if (variant == 2 && L > 1)
+    mgs_kernel<L, L != 1><<<(unsigned)((n_sys + 31) / 32), 32, 0, st>>>(A, R, x, rows, cols, n_sys);
+  else
+    mgs_kernel<L, false><<<(unsigned)((n_sys + 31) / 32), 32, 0, st>>>(A, R, x, rows, cols, n_sys);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HT_OK : cuda_fail(e, "mgs launch");
 }
@@ -727,7 +814,7 @@ int track_occupancy_l(int team) {
 #error "compile once per precision with -DHT_LIMBS=1, 2 or 4"
 #endif
 template int launch_start_l<HT_LIMBS>(int, const int32_t*, int64_t, int64_t, double*, cudaStream_t);
-template int launch_mgs_l<HT_LIMBS>(double*, double*, double*, int, int, int64_t, cudaStream_t);
+template int launch_mgs_l<HT_LIMBS>(double*, double*, double*, int, int, int64_t, int, cudaStream_t);
 template int launch_init_l<HT_LIMBS>(const TrackArgs&, cudaStream_t);
 template int launch_track_l<HT_LIMBS>(const TrackArgs&, int, int64_t, cudaStream_t);
 template int track_occupancy_l<HT_LIMBS>(int);

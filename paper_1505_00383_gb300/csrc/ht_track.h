@@ -85,7 +85,7 @@ struct TrackArgs {
 template <int L>
 int launch_start_l(int n, const int32_t* d_deg, int64_t first, int64_t count, double* x, cudaStream_t st);
 template <int L>
-int launch_mgs_l(double* A, double* R, double* x, int rows, int cols, int64_t n_sys, cudaStream_t st);
+int launch_mgs_l(double* A, double* R, double* x, int rows, int cols, int64_t n_sys, int variant, cudaStream_t st);
 template <int L>
 int launch_init_l(const TrackArgs& a, cudaStream_t st);
 template <int L>

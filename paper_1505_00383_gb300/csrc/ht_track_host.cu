@@ -148,15 +148,24 @@ int ht_start_solutions(int n, const int32_t* degrees, int limbs, int64_t first, 
 }
 
 int ht_mgs_solve(int limbs, int rows, int cols, int64_t n_sys, double* Ab, double* R, double* x, void* stream) {
+  return ht_mgs_solve_ex(limbs, 0, rows, cols, n_sys, Ab, R, x, stream);
+}
+
+int ht_mgs_solve_ex(int limbs, int variant, int rows, int cols, int64_t n_sys, double* Ab, double* R, double* x,
+                    void* stream) {
   clear_error();
   if (rows < 1 || cols < 1 || rows < cols || n_sys < 0)
     return set_error(HT_EINVAL, "ht_mgs_solve: need rows >= cols >= 1, n_sys >= 0");
+  if (variant != 0 && variant != 2) return set_error(HT_EINVAL, "ht_mgs_solve_ex: variant %d (0 or 2)", variant);
+  if (variant == 2 && (limbs == 1 || rows > 64))
+    return set_error(HT_EUNSUPPORTED, "ht_mgs_solve_ex: integer limbs need DD or QD and at most 64 rows");
   if (n_sys == 0) return HT_OK;
   if (!Ab || !R || !x || (((uintptr_t)Ab | (uintptr_t)R | (uintptr_t)x) & 7) || !is_device_ptr(Ab) ||
       !is_device_ptr(R) || !is_device_ptr(x))
     return set_error(HT_EINVAL, "ht_mgs_solve: buffers must be device memory");
   cudaStream_t st = (cudaStream_t)stream;
-  return by_limbs(limbs, [&](auto c) { return launch_mgs_l<decltype(c)::value>(Ab, R, x, rows, cols, n_sys, st); });
+  return by_limbs(limbs,
+                  [&](auto c) { return launch_mgs_l<decltype(c)::value>(Ab, R, x, rows, cols, n_sys, variant, st); });
 }
 
 int ht_compact(const int8_t* status, int64_t m, int32_t* path_idx, int32_t* count, void* stream) {
@@ -260,9 +269,10 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.coef = s->d_coef;
   a.cfz = s->d_coef_fz;
   a.clg = s->d_coef_lg;
-  // DD and QD evaluate f on the integer pipe unless an FP64 evaluation variant
-  // was chosen for this system (ht_set_eval_config 0 or 1)
-  a.int_eval = L > 1 && s->d_coef_fz && n <= 64 && s->max_k <= 64 && (s->eval_variant == -1 || s->eval_variant == 2);
+  // DD and QD (n <= 32) evaluate f and solve the Newton systems on the
+  // integer pipe unless an FP64 variant was chosen for this system
+  // (ht_set_eval_config 0 or 1)
+  a.int_eval = L > 1 && s->d_coef_fz && n <= 32 && (s->eval_variant == -1 || s->eval_variant == 2);
   a.deg = (const int32_t*)(w + o_deg);
   a.gamma_re = gamma[0];
   a.gamma_im = gamma[1];

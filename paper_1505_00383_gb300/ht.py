@@ -43,6 +43,7 @@ SIGNATURES = {
     "ht_default_params": ([I32, P], I32),
     "ht_start_solutions": ([I32, P, I32, I64, I64, P, P], I32),
     "ht_mgs_solve": ([I32, I32, I32, I64, P, P, P, P], I32),
+    "ht_mgs_solve_ex": ([I32, I32, I32, I32, I64, P, P, P, P], I32),
     "ht_compact": ([P, I64, P, P, P], I32),
     "ht_compact_noalloc": ([P, I64, P, P, P], I32),
     "ht_track_paths": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P], I32),
@@ -236,6 +237,10 @@ def ht_start_solutions(n, degrees, limbs, first, count, x0, stream=None) -> None
 
 def ht_mgs_solve(limbs, rows, cols, n_sys, Ab, R, x, stream=None) -> None:
     _check(lib().ht_mgs_solve(limbs, rows, cols, n_sys, _ptr(Ab), _ptr(R), _ptr(x), _stream(stream)))
+
+
+def ht_mgs_solve_ex(limbs, variant, rows, cols, n_sys, Ab, R, x, stream=None) -> None:
+    _check(lib().ht_mgs_solve_ex(limbs, variant, rows, cols, n_sys, _ptr(Ab), _ptr(R), _ptr(x), _stream(stream)))
 
 
 def ht_compact(status, m, path_idx, count, stream=None) -> None:

@@ -2,6 +2,7 @@
 // for CPU tests of that arithmetic against the oracle.
 #include <cstdint>
 #include <cstdio>
+#include <vector>
 
 #include "../paper_1505_00383_gb300/csrc/ht_mpi.cuh"
 #include "../paper_1505_00383_gb300/csrc/ht_mpi_ops.cuh"
@@ -262,5 +263,59 @@ extern "C" int mpi_invsqrt(int L, int64_t n, const double* v, double* out) {
   else if (L == 2) invsqrt<5, 2>(n, v, out, 2);
   else if (L == 4) invsqrt<8, 4>(n, v, out, 3);
   else return -1;
+  return 0;
+}
+
+// ---- least squares by modified Gram-Schmidt on limb strings (one system)
+template <int W, int L>
+static void mgs_seq(int rows, int cols, const double* Ab, double* x) {
+  constexpr int N = 64;
+  using Z = fz<W>;
+  const int C = cols + 1;
+  std::vector<Z> A((size_t)rows * C), col(rows), Q(rows), scratch(rows), R((size_t)cols * C);
+  for (int i = 0; i < rows; ++i)
+    for (int j = 0; j < C; ++j) {
+      const double* e = Ab + ((size_t)i * C + j) * 2 * L;
+      A[(size_t)i * C + j] = from_doubles<W, L>(e, e + L);
+    }
+  auto column = [&](int j, std::vector<Z>& out) {
+    for (int i = 0; i < rows; ++i) out[i] = A[(size_t)i * C + j];
+  };
+  auto put = [&](int j, const std::vector<Z>& in) {
+    for (int i = 0; i < rows; ++i) A[(size_t)i * C + j] = in[i];
+  };
+  for (int q = 0; q < cols; ++q) {
+    column(q, Q);
+    Z nrm = norm2<W, N>(Q.data(), rows, scratch.data());
+    Z inv = inv_sqrt<W>(nrm, inv_sqrt_steps<W>());
+    for (int i = 0; i < rows; ++i) Q[i] = mul<W>(Q[i], inv);
+    put(q, Q);
+    R[(size_t)q * C + q] = inv;
+    for (int j = q + 1; j < C; ++j) {
+      column(j, col);
+      Z r = dot_conj<W, N>(Q.data(), col.data(), rows, scratch.data());
+      R[(size_t)q * C + j] = r;
+      sub_scaled<W>(col.data(), r, Q.data(), rows);
+      put(j, col);
+    }
+  }
+  std::vector<Z> X(cols), terms(cols + 1);
+  for (int q = cols - 1; q >= 0; --q) {
+    int k = 0;
+    terms[k++] = R[(size_t)q * C + cols];
+    for (int j = q + 1; j < cols; ++j) terms[k++] = mul<W>(R[(size_t)q * C + j], X[j]);
+    X[q] = mul<W>(first_minus_rest<W, N + 1>(terms.data(), k), R[(size_t)q * C + q]);
+  }
+  for (int q = 0; q < cols; ++q) to_doubles<W, L>(X[q], x + (size_t)q * 2 * L, x + (size_t)q * 2 * L + L);
+}
+extern "C" int mpi_mgs(int L, int rows, int cols, int64_t n_sys, const double* Ab, double* x) {
+  if (rows < cols || cols < 1 || rows > 64) return -1;
+  const size_t sa = (size_t)rows * (cols + 1) * 2 * L, sx = (size_t)cols * 2 * L;
+  for (int64_t s = 0; s < n_sys; ++s) {
+    if (L == 2) mgs_seq<5, 2>(rows, cols, Ab + s * sa, x + s * sx);
+    else if (L == 4) mgs_seq<8, 4>(rows, cols, Ab + s * sa, x + s * sx);
+    else if (L == 1) mgs_seq<3, 1>(rows, cols, Ab + s * sa, x + s * sx);
+    else return -1;
+  }
   return 0;
 }

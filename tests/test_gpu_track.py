@@ -41,9 +41,12 @@ def test_start_solutions_match_oracle(ht, L, degrees):
     assert np.max(e) <= {1: 4e-16, 2: 1e-31, 4: 1e-62}[L], np.max(e)
 
 
-@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("L,variant", [(1, 0), (2, 0), (4, 0), (2, 2), (4, 2)])
 @pytest.mark.parametrize("rows,cols", [(6, 6), (12, 12), (9, 5), (1, 1)])
-def test_mgs_solve_matches_oracle(ht, L, rows, cols):
+def test_mgs_solve_matches_oracle(ht, L, variant, rows, cols):
+    """Both arithmetics against the oracle's MGS, within the conditioning
+    bound at the variant's unit (2^-53L; for QD integer limbs the 204 bits a
+    product keeps)."""
     rng = synth.SplitMix64(300 + rows * 7 + cols + L)
     n_sys = 37  # a full warp of systems and a ragged tail
     re, im = synth.unit_circle(rng, n_sys * rows * (cols + 1))
@@ -57,16 +60,17 @@ def test_mgs_solve_matches_oracle(ht, L, rows, cols):
     dAb = dev(Ab)
     dR = torch.empty((cols, cols + 1, 2, L, n_sys), dtype=torch.float64, device="cuda")
     dx = torch.empty((cols, 2, L, n_sys), dtype=torch.float64, device="cuda")
-    ht.ht_mgs_solve(L, rows, cols, n_sys, dAb, dR, dx)
+    ht.ht_mgs_solve_ex(L, variant, rows, cols, n_sys, dAb, dR, dx)
     torch.cuda.synchronize()
     got = dx.cpu().numpy()
+    unit = 2.0 ** (-53 * L) if variant == 0 else 2.0 ** -min(53 * L, 29 * ({2: 5, 4: 8}[L] - 1) + 1)
     refv = np.ascontiguousarray(ref.transpose(1, 2, 3, 0))
     for s in range(n_sys):
         Ad = Ab[:, :cols, 0, 0, s] + 1j * Ab[:, :cols, 1, 0, s]
         cond = np.linalg.cond(Ad)
         scale = np.max(np.abs(refv[:, 0, 0, s] + 1j * refv[:, 1, 0, s]))
         e = np.max(cerr(got[..., s:s + 1], refv[..., s:s + 1]))
-        assert e <= 64 * cond * cond * 2.0 ** (-53 * L) * scale * rows, (s, e, cond)
+        assert e <= 64 * cond * cond * unit * scale * rows, (s, e, cond)
 
 
 def test_compaction_table_tabjobidx(ht):

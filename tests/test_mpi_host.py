@@ -216,3 +216,29 @@ def test_inverse_square_root_against_oracle(oracle_lib, shim, L):
     ref = oracle_lib.real_op("div", np.tile(np.eye(1, L), (v.shape[0], 1)), oracle_lib.real_op("sqrt", v))
     d = oracle_lib.value_diff(out, ref)
     assert np.all(np.abs(d) <= _unit(L) * 32 * np.abs(ref[:, 0])), np.max(np.abs(d) / np.abs(ref[:, 0]))
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("rows,cols", [(6, 6), (12, 12), (9, 5), (1, 1)])
+def test_least_squares_on_limb_strings_matches_oracle(oracle_lib, shim, L, rows, cols):
+    """Modified Gram-Schmidt with every dot product and norm as one exact
+    fixed-point sum, 1/sqrt by Newton: the solution of [A | b] against the
+    oracle's MGS within the conditioning bound of the GPU test."""
+    shim.mpi_mgs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+    rng = synth.SplitMix64(300 + rows * 7 + cols + L)
+    n_sys = 12
+    re, im = synth.unit_circle(rng, n_sys * rows * (cols + 1))
+    mag = rng.uniform(re.size) + 0.5
+    Ab = np.zeros((n_sys, rows, cols + 1, 2, L))
+    Ab[..., 0, :] = synth.random_tails(rng, (re * mag), L).T.reshape(n_sys, rows, cols + 1, L)
+    Ab[..., 1, :] = synth.random_tails(rng, (im * mag), L).T.reshape(n_sys, rows, cols + 1, L)
+    x = np.empty((n_sys, cols, 2, L))
+    assert shim.mpi_mgs(L, rows, cols, n_sys, _p(np.ascontiguousarray(Ab)), _p(x)) == 0
+    ref = oracle_lib.mgs_solve(np.ascontiguousarray(Ab[:, :, :cols]), np.ascontiguousarray(Ab[:, :, cols]))
+    for s in range(n_sys):
+        Ad = Ab[s, :, :cols, 0, 0] + 1j * Ab[s, :, :cols, 1, 0]
+        cond = np.linalg.cond(Ad)
+        r = ref[s, :, 0, 0] + 1j * ref[s, :, 1, 0]
+        scale = np.max(np.abs(r))
+        e = np.max(_cerr(oracle_lib, x[s], ref[s]))
+        assert e <= 64 * cond * cond * _unit(L) * scale * rows, (s, e, cond)
