@@ -65,8 +65,9 @@ def eval_ops_per_point(system, L):
 
 
 # Limb products (32x32 -> 64-bit multiply-adds) per complex multiplication of
-# the integer variant (paper_1505_00383_gb300/csrc/ht_mpi.cuh): 4 real
-# products, each over the limb pairs whose column is kept (x + y >= W - 2).
+# the integer variant (paper_1505_00383_gb300/csrc/ht_mpi.cuh): 3 real
+# products (Gauss's form), each over the limb pairs whose column is kept
+# (x + y >= W - 2).
 INT_W = {1: 3, 2: 5, 4: 8}
 
 
@@ -79,7 +80,7 @@ def int_products_per_point(system, L):
         k = a.size
         if k:
             tot += int((a - 1).sum()) + (1 if k == 1 else 3 * k - 3)
-    return tot * 4 * pairs
+    return tot * 3 * pairs
 
 
 def _args():

@@ -81,7 +81,7 @@ static int launch_v(const EvalArgs& a, int threads, cudaStream_t st) {
 //      in place in the output (2L doubles hold exactly 2 x 2L int32 limbs);
 //   4. converts the accumulators to L doubles.
 template <int L>
-__global__ void __launch_bounds__(128) evaldiff_int_kernel(EvalArgs a, const mpi::fz<IntW<L>::W>* __restrict__ cfz,
+__global__ void __launch_bounds__(128, 4) evaldiff_int_kernel(EvalArgs a, const mpi::fz<IntW<L>::W>* __restrict__ cfz,
                                                            const float* __restrict__ clg) {
   using Z = mpi::fz<IntW<L>::W>;
   Z X[kIntMaxVars];

@@ -41,7 +41,7 @@ template <int L>
 struct RowAcc {
   double* jrow;
   int64_t n, p;
-  __device__ __noinline__ void add(int v, const mpi::fz<IntW<L>::W>& d, int e, int F) {
+  __device__ __forceinline__ void add(int v, const mpi::fz<IntW<L>::W>& d, int e, int F) {
     constexpr int WA = IntW<L>::WA;
     int32_t ar[WA], ai[WA];
     ld_fix<L>(jrow, v, n, p, ar, ai);

@@ -203,24 +203,36 @@ template <int W>
 HT_HD fz<W> mul(const fz<W>& a, const fz<W>& b) {
   constexpr int C0 = W - 2 > 0 ? W - 2 : 0;  // lowest column kept
   constexpr int NC = 2 * W - C0;             // columns C0 .. 2W-1
-  int64_t cr[NC], ci[NC], cr2[NC], ci2[NC];
+  // Three real limb products per column (Gauss): re = ar br - ai bi,
+  // im = (ar + ai)(br + bi) - ar br - ai bi.  The operand sums have limbs
+  // below 2^30, so a column of at most W products stays below 2^63; the
+  // columns are summed modulo 2^64 (unsigned) and the exact column values,
+  // which fit in int64, come out of the subtraction -- the same integers as
+  // the four-product form.
+  int32_t sa[W], sb[W];
 #pragma unroll
-  for (int c = 0; c < NC; ++c) cr[c] = ci[c] = cr2[c] = ci2[c] = 0;
+  for (int x = 0; x < W; ++x) {
+    sa[x] = a.r[x] + a.i[x];
+    sb[x] = b.r[x] + b.i[x];
+  }
+  uint64_t c1[NC], c2[NC], c3[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) c1[c] = c2[c] = c3[c] = 0;
 #pragma unroll
   for (int x = 0; x < W; ++x)
 #pragma unroll
     for (int y = 0; y < W; ++y) {
       if (x + y < C0) continue;
       const int c = x + y - C0;
-      cr[c] += (int64_t)a.r[x] * b.r[y];
-      cr2[c] += (int64_t)a.i[x] * b.i[y];
-      ci[c] += (int64_t)a.r[x] * b.i[y];
-      ci2[c] += (int64_t)a.i[x] * b.r[y];
+      c1[c] += (uint64_t)((int64_t)a.r[x] * b.r[y]);
+      c2[c] += (uint64_t)((int64_t)a.i[x] * b.i[y]);
+      c3[c] += (uint64_t)((int64_t)sa[x] * sb[y]);
     }
+  int64_t cr[NC], ci[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) {
-    cr[c] -= cr2[c];
-    ci[c] += ci2[c];
+    cr[c] = (int64_t)(c1[c] - c2[c]);
+    ci[c] = (int64_t)(c3[c] - c1[c] - c2[c]);
   }
   carry<NC>(cr);
   carry<NC>(ci);

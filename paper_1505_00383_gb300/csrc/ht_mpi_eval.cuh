@@ -73,61 +73,115 @@ HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const f
   return frame_of<WA>(E, cnt);
 }
 
-// The complex product as called from the sweep.  On the device the 5- and
-// 8-limb products (a few hundred instructions each when unrolled) run out of
-// line, one copy for all call sites, so the sweep's code stays within the
-// instruction cache.
-#if defined(__CUDA_ARCH__)
-template <int W>
-__device__ __noinline__ fz<W> mul_ool(const fz<W>& a, const fz<W>& b) {
-  return mul<W>(a, b);
-}
-#endif
-template <int W>
-HT_HD fz<W> mul_sw(const fz<W>& a, const fz<W>& b) {
-#if defined(__CUDA_ARCH__)
-  if constexpr (W >= 5) return mul_ool<W>(a, b);
-#endif
-  return mul<W>(a, b);
-}
-
 // Value (fixed-point vr, vi in frame F) and gradient (through acc.add(var, d,
 // e, Fv[var])) of the monomials m0..m1 at the point X (converted variables);
 // P is scratch for k forward products.
+//
+// The reverse-mode sweep of one monomial c x_{v_0}^{a_0} ... x_{v_{k-1}}^{a_{k-1}}
+// is a sequence of steps, each at most one product followed by one action:
+//   common factor  cf <- cf x_{v_r}              (a_r - 1 times for each r)
+//   forward        P_r <- (r ? P_{r-1} : cf) x_{v_r};  value += P_{k-1}
+//   backward       d_{k-1} = P_{k-2}; S = x_{v_{k-1}};
+//                  for r = k-2 .. 1: d_r = P_{r-1} S, S <- S x_{v_r};
+//                  d_0 = cf S                     (k = 1: d_0 = cf)
+// with every d_r added into the row as a_r d_r.  The loop runs the steps of a
+// monomial through a single product and a single accumulation site, so the
+// multi-limb product is emitted once (the 8-limb product is several hundred
+// instructions) and its operands stay in registers.
 template <int L, class Acc>
 HT_HD void eval_poly_int(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m0, int m1,
                          const fz<IntW<L>::W>* X, int F, const int* Fv, Acc& acc, int32_t* vr, int32_t* vi,
                          fz<IntW<L>::W>* P) {
   constexpr int W = IntW<L>::W, WA = IntW<L>::WA;
   using Z = fz<W>;
+  enum : int { CHAIN, FWD, BWD0, BWD_D, BWD_S, LAST, DONE };
   for (int m = m0; m < m1; ++m) {
     const int beg = mon_off[m], k = mon_off[m + 1] - beg;
     const uint16_t* pr = pairs + beg;
-    Z cf = cfz[m];
-    for (int r = 0; r < k; ++r) {
-      const uint16_t q = pr[r];
-      for (int e = 1; e < (q >> 8); ++e) cf = mul_sw<W>(cf, X[q & 0xff]);
-    }
+    Z cf = cfz[m], S = cf;
     if (k == 0) {
       acc_add_fast<W, WA>(vr, vi, cf, 1, F);
       continue;
     }
-    for (int r = 0; r < k; ++r) P[r] = mul_sw<W>(r == 0 ? cf : P[r - 1], X[pr[r] & 0xff]);
-    acc_add_fast<W, WA>(vr, vi, P[k - 1], 1, F);
-    if (k == 1) {
-      acc.add(pr[0] & 0xff, cf, pr[0] >> 8, Fv[pr[0] & 0xff]);
-      continue;
+    int phase = CHAIN, r = 0, e = 1;
+    while (phase != DONE) {
+      // the step: operands, whether to multiply, and the action
+      Z lhs, rhs;
+      bool prod = true;
+      int act = 0;  // 0 cf, 1 P[r] (+ value at r = k - 1), 2 S, 3 row entry of var
+      int var = 0, ex = 1;
+      if (phase == CHAIN) {
+        while (r < k && e >= (pr[r] >> 8)) {  // next variable with exponent left
+          ++r;
+          e = 1;
+        }
+        if (r == k) {
+          phase = FWD;
+          r = 0;
+          continue;
+        }
+        lhs = cf;
+        rhs = X[pr[r] & 0xff];
+        act = 0;
+        ++e;
+      } else if (phase == FWD) {
+        lhs = r == 0 ? cf : P[r - 1];
+        rhs = X[pr[r] & 0xff];
+        act = 1;
+      } else if (phase == BWD0) {  // d_{k-1} = P_{k-2} (k >= 2) or d_0 = cf (k = 1)
+        lhs = k == 1 ? cf : P[k - 2];
+        prod = false;
+        act = 3;
+        var = pr[k - 1] & 0xff;
+        ex = pr[k - 1] >> 8;
+      } else if (phase == BWD_D) {
+        lhs = P[r - 1];
+        rhs = S;
+        act = 3;
+        var = pr[r] & 0xff;
+        ex = pr[r] >> 8;
+      } else if (phase == BWD_S) {
+        lhs = S;
+        rhs = X[pr[r] & 0xff];
+        act = 2;
+      } else {  // LAST: d_0 = cf S
+        lhs = cf;
+        rhs = S;
+        act = 3;
+        var = pr[0] & 0xff;
+        ex = pr[0] >> 8;
+      }
+      const Z t = prod ? mul<W>(lhs, rhs) : lhs;
+      if (act == 0) {
+        cf = t;
+      } else if (act == 1) {
+        P[r] = t;
+        if (r == k - 1) acc_add_fast<W, WA>(vr, vi, t, 1, F);
+      } else if (act == 2) {
+        S = t;
+      } else {
+        acc.add(var, t, ex, Fv[var]);
+      }
+      // next step
+      if (phase == FWD) {
+        if (++r == k) phase = BWD0;
+      } else if (phase == BWD0) {
+        if (k == 1) {
+          phase = DONE;
+        } else {
+          S = X[pr[k - 1] & 0xff];
+          r = k - 2;
+          phase = r >= 1 ? BWD_D : LAST;
+        }
+      } else if (phase == BWD_D) {
+        phase = BWD_S;
+      } else if (phase == BWD_S) {
+        --r;
+        phase = r >= 1 ? BWD_D : LAST;
+      } else if (phase == LAST) {
+        phase = DONE;
+      }
     }
-    uint16_t q = pr[k - 1];
-    acc.add(q & 0xff, P[k - 2], q >> 8, Fv[q & 0xff]);
-    Z S = X[q & 0xff];
-    for (int r = k - 2; r >= 1; --r) {
-      q = pr[r];
-      acc.add(q & 0xff, mul_sw<W>(P[r - 1], S), q >> 8, Fv[q & 0xff]);
-      S = mul_sw<W>(S, X[q & 0xff]);
-    }
-    q = pr[0];
-    acc.add(q & 0xff, mul_sw<W>(cf, S), q >> 8, Fv[q & 0xff]);
   }
 }
 
