@@ -69,6 +69,7 @@ def eval_ops_per_point(system, L):
 # products (Gauss's form), each over the limb pairs whose column is kept
 # (x + y >= W - 2).
 INT_W = {1: 3, 2: 5, 4: 8}
+VARIANT_NAMES = {0: "unrolled fp64", 1: "compact fp64", 2: "integer limbs"}
 
 
 def int_products_per_point(system, L):
@@ -363,12 +364,12 @@ def run_ours(a):
     for L in PRECISIONS:  # autotuner: kernel body and CTA size per precision (part of warm-up)
         v, t, ms = ht.ht_tune_eval(sys_h[L], n, xs[L], vals[L], jacs[L], reps=1)
         variant[L] = v
-        tuned[NAMES[L]] = {"variant": {0: "unrolled fp64", 1: "compact fp64", 2: "integer limbs"}[v], "threads": t}
+        tuned[NAMES[L]] = {"variant": VARIANT_NAMES[v], "threads": t}
     # where the integer variant won, one launch of the FP64 bodies for reference
     # (FP64-pipe utilisation of the error-free DD/QD arithmetic)
     fp64_ref = {}
     for L in PRECISIONS:
-        if variant[L] == 2:
+        if variant[L] >= 2:
             ht.ht_set_eval_config(sys_h[L], 1, 256)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.zero_()
@@ -377,7 +378,7 @@ def run_ours(a):
             e1.record(stream)
             torch.cuda.synchronize()
             fp64_ref[L] = e0.elapsed_time(e1)
-            ht.ht_set_eval_config(sys_h[L], 2, tuned[NAMES[L]]["threads"])
+            ht.ht_set_eval_config(sys_h[L], variant[L], tuned[NAMES[L]]["threads"])
 
     def step(events=None):
         for L in PRECISIONS:
@@ -440,7 +441,7 @@ def run_ours(a):
     dom = max(PRECISIONS, key=lambda L: statistics.mean(launch_ms[L]))
     dom_ms = statistics.mean(launch_ms[dom])
     tr = _traffic(dom)
-    if variant[dom] == 2:
+    if variant[dom] >= 2:
         work = int_products_per_point(system, dom) * n
         achieved = work / (dom_ms * 1e-3)
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_peak / 1e12,
@@ -461,7 +462,7 @@ def run_ours(a):
         m = statistics.mean(launch_ms[L])
         d = {"ms": m, "pts_per_s": n / (m * 1e-3), "variant": tuned[NAMES[L]]["variant"],
              "out_GB_per_s": (system.n_polys * (system.n_vars + 1) * 16 * L * n) / (m * 1e-3) / 1e9}
-        if variant[L] == 2:
+        if variant[L] >= 2:
             d["imad_frac"] = int_products_per_point(system, L) * n / (m * 1e-3) / imad_peak
             if L in fp64_ref:
                 d["fp64_bodies"] = {"ms": fp64_ref[L], "pts_per_s": n / (fp64_ref[L] * 1e-3),

@@ -73,9 +73,9 @@ HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const f
   return frame_of<WA>(E, cnt);
 }
 
-// Value (fixed-point vr, vi in frame F) and gradient (through acc.add(var, d,
-// e, Fv[var])) of the monomials m0..m1 at the point X (converted variables);
-// P is scratch for k forward products.
+// Value (through val_add(term)) and gradient (through acc.add(var, d, e,
+// Fv[var])) of monomial m at the point X (converted variables); P is scratch
+// for k forward products.
 //
 // The reverse-mode sweep of one monomial c x_{v_0}^{a_0} ... x_{v_{k-1}}^{a_{k-1}}
 // is a sequence of steps, each at most one product followed by one action:
@@ -84,105 +84,120 @@ HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const f
 //   backward       d_{k-1} = P_{k-2}; S = x_{v_{k-1}};
 //                  for r = k-2 .. 1: d_r = P_{r-1} S, S <- S x_{v_r};
 //                  d_0 = cf S                     (k = 1: d_0 = cf)
-// with every d_r added into the row as a_r d_r.  The loop runs the steps of a
-// monomial through a single product and a single accumulation site, so the
-// multi-limb product is emitted once (the 8-limb product is several hundred
-// instructions) and its operands stay in registers.
+// with every d_r added into the row as a_r d_r (acc.add) and the value through
+// val_add.  The loop runs the steps of a monomial through a single product
+// and a single accumulation site, so the multi-limb product is emitted once
+// (the 8-limb product is several hundred instructions) and its operands stay
+// in registers.
+template <int L, class Acc, class ValAdd>
+HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m,
+                          const fz<IntW<L>::W>* X, const int* Fv, Acc& acc, ValAdd& val_add, fz<IntW<L>::W>* P) {
+  constexpr int W = IntW<L>::W;
+  using Z = fz<W>;
+  enum : int { CHAIN, FWD, BWD0, BWD_D, BWD_S, LAST, DONE };
+  const int beg = mon_off[m], k = mon_off[m + 1] - beg;
+  const uint16_t* pr = pairs + beg;
+  Z cf = cfz[m], S = cf;
+  if (k == 0) {
+    val_add(cf);
+    return;
+  }
+  int phase = CHAIN, r = 0, e = 1;
+  while (phase != DONE) {
+    // the step: operands, whether to multiply, and the action
+    Z lhs, rhs;
+    bool prod = true;
+    int act = 0;  // 0 cf, 1 P[r] (+ value at r = k - 1), 2 S, 3 row entry of var
+    int var = 0, ex = 1;
+    if (phase == CHAIN) {
+      while (r < k && e >= (pr[r] >> 8)) {  // next variable with exponent left
+        ++r;
+        e = 1;
+      }
+      if (r == k) {
+        phase = FWD;
+        r = 0;
+        continue;
+      }
+      lhs = cf;
+      rhs = X[pr[r] & 0xff];
+      act = 0;
+      ++e;
+    } else if (phase == FWD) {
+      lhs = r == 0 ? cf : P[r - 1];
+      rhs = X[pr[r] & 0xff];
+      act = 1;
+    } else if (phase == BWD0) {  // d_{k-1} = P_{k-2} (k >= 2) or d_0 = cf (k = 1)
+      lhs = k == 1 ? cf : P[k - 2];
+      prod = false;
+      act = 3;
+      var = pr[k - 1] & 0xff;
+      ex = pr[k - 1] >> 8;
+    } else if (phase == BWD_D) {
+      lhs = P[r - 1];
+      rhs = S;
+      act = 3;
+      var = pr[r] & 0xff;
+      ex = pr[r] >> 8;
+    } else if (phase == BWD_S) {
+      lhs = S;
+      rhs = X[pr[r] & 0xff];
+      act = 2;
+    } else {  // LAST: d_0 = cf S
+      lhs = cf;
+      rhs = S;
+      act = 3;
+      var = pr[0] & 0xff;
+      ex = pr[0] >> 8;
+    }
+    const Z t = prod ? mul<W>(lhs, rhs) : lhs;
+    if (act == 0) {
+      cf = t;
+    } else if (act == 1) {
+      P[r] = t;
+      if (r == k - 1) val_add(t);
+    } else if (act == 2) {
+      S = t;
+    } else {
+      acc.add(var, t, ex, Fv[var]);
+    }
+    // next step
+    if (phase == FWD) {
+      if (++r == k) phase = BWD0;
+    } else if (phase == BWD0) {
+      if (k == 1) {
+        phase = DONE;
+      } else {
+        S = X[pr[k - 1] & 0xff];
+        r = k - 2;
+        phase = r >= 1 ? BWD_D : LAST;
+      }
+    } else if (phase == BWD_D) {
+      phase = BWD_S;
+    } else if (phase == BWD_S) {
+      --r;
+      phase = r >= 1 ? BWD_D : LAST;
+    } else if (phase == LAST) {
+      phase = DONE;
+    }
+  }
+}
+
+// Multiplications of one monomial's sweep (for balancing work over lanes).
+HT_HD int sweep_products(const uint16_t* pr, int k) {
+  int c = 0;
+  for (int r = 0; r < k; ++r) c += (pr[r] >> 8) - 1;
+  return k == 0 ? 0 : c + (k == 1 ? 1 : 3 * k - 3);
+}
+
+// Value (fixed-point vr, vi in frame F) and gradient of the monomials m0..m1.
 template <int L, class Acc>
 HT_HD void eval_poly_int(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m0, int m1,
                          const fz<IntW<L>::W>* X, int F, const int* Fv, Acc& acc, int32_t* vr, int32_t* vi,
                          fz<IntW<L>::W>* P) {
   constexpr int W = IntW<L>::W, WA = IntW<L>::WA;
-  using Z = fz<W>;
-  enum : int { CHAIN, FWD, BWD0, BWD_D, BWD_S, LAST, DONE };
-  for (int m = m0; m < m1; ++m) {
-    const int beg = mon_off[m], k = mon_off[m + 1] - beg;
-    const uint16_t* pr = pairs + beg;
-    Z cf = cfz[m], S = cf;
-    if (k == 0) {
-      acc_add_fast<W, WA>(vr, vi, cf, 1, F);
-      continue;
-    }
-    int phase = CHAIN, r = 0, e = 1;
-    while (phase != DONE) {
-      // the step: operands, whether to multiply, and the action
-      Z lhs, rhs;
-      bool prod = true;
-      int act = 0;  // 0 cf, 1 P[r] (+ value at r = k - 1), 2 S, 3 row entry of var
-      int var = 0, ex = 1;
-      if (phase == CHAIN) {
-        while (r < k && e >= (pr[r] >> 8)) {  // next variable with exponent left
-          ++r;
-          e = 1;
-        }
-        if (r == k) {
-          phase = FWD;
-          r = 0;
-          continue;
-        }
-        lhs = cf;
-        rhs = X[pr[r] & 0xff];
-        act = 0;
-        ++e;
-      } else if (phase == FWD) {
-        lhs = r == 0 ? cf : P[r - 1];
-        rhs = X[pr[r] & 0xff];
-        act = 1;
-      } else if (phase == BWD0) {  // d_{k-1} = P_{k-2} (k >= 2) or d_0 = cf (k = 1)
-        lhs = k == 1 ? cf : P[k - 2];
-        prod = false;
-        act = 3;
-        var = pr[k - 1] & 0xff;
-        ex = pr[k - 1] >> 8;
-      } else if (phase == BWD_D) {
-        lhs = P[r - 1];
-        rhs = S;
-        act = 3;
-        var = pr[r] & 0xff;
-        ex = pr[r] >> 8;
-      } else if (phase == BWD_S) {
-        lhs = S;
-        rhs = X[pr[r] & 0xff];
-        act = 2;
-      } else {  // LAST: d_0 = cf S
-        lhs = cf;
-        rhs = S;
-        act = 3;
-        var = pr[0] & 0xff;
-        ex = pr[0] >> 8;
-      }
-      const Z t = prod ? mul<W>(lhs, rhs) : lhs;
-      if (act == 0) {
-        cf = t;
-      } else if (act == 1) {
-        P[r] = t;
-        if (r == k - 1) acc_add_fast<W, WA>(vr, vi, t, 1, F);
-      } else if (act == 2) {
-        S = t;
-      } else {
-        acc.add(var, t, ex, Fv[var]);
-      }
-      // next step
-      if (phase == FWD) {
-        if (++r == k) phase = BWD0;
-      } else if (phase == BWD0) {
-        if (k == 1) {
-          phase = DONE;
-        } else {
-          S = X[pr[k - 1] & 0xff];
-          r = k - 2;
-          phase = r >= 1 ? BWD_D : LAST;
-        }
-      } else if (phase == BWD_D) {
-        phase = BWD_S;
-      } else if (phase == BWD_S) {
-        --r;
-        phase = r >= 1 ? BWD_D : LAST;
-      } else if (phase == LAST) {
-        phase = DONE;
-      }
-    }
-  }
+  auto val_add = [&](const fz<W>& t) { acc_add_fast<W, WA>(vr, vi, t, 1, F); };
+  for (int m = m0; m < m1; ++m) sweep_monomial<L>(mon_off, pairs, cfz, m, X, Fv, acc, val_add, P);
 }
 
 }  // namespace mpi
