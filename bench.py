@@ -239,8 +239,10 @@ def _agreement(A, B, tol=1e-10):
 # precisions, the training systems (same shape, other seeds; traces and
 # probes in double) and the held-out system tracked by both arms
 LEARNED_CASES = {
-    "c3_learned_d": dict(limbs=1, check_limbs=2, eval_seed=3500, train_seeds=range(3000, 3006), warm_paths=None),
-    "c4_stress_qd": dict(limbs=4, check_limbs=0, eval_seed=4000, train_seeds=range(4100, 4106), warm_paths=1024),
+    "c3_learned_d": dict(limbs=1, check_limbs=2, eval_seed=3500, train_seeds=range(3000, 3006), warm_paths=None,
+                         tune_paths=4096),
+    "c4_stress_qd": dict(limbs=4, check_limbs=0, eval_seed=4000, train_seeds=range(4100, 4106), warm_paths=1024,
+                         tune_paths=1024),
 }
 
 
@@ -267,6 +269,9 @@ def learned_vs_plain(ht, torch, world, name, m, train_paths=256):
     train_s = time.perf_counter() - t0
     s = synth.config_system(name, case["eval_seed"])
     g = synth.random_gamma(case["eval_seed"])
+    # launch shape from the autotuner (plain rule, a sample of the paths); both arms use it
+    team, iters, _ = ht.ht_tune_track(ht.system_from(s, L), s.degrees(), g, case["tune_paths"], prm)
+    prm.team_warps, prm.iters_per_launch = team, iters
     out = {}
     for arm, nn in (("plain", None), ("learned", net)):
         learned.track(s, L, g, case["warm_paths"] or m, prm, net=nn, check_limbs=CL)  # warm-up: workspace, graphs
@@ -296,6 +301,8 @@ def learned_vs_plain(ht, torch, world, name, m, train_paths=256):
            "rejects_per_path": {"plain": ra["stats"]["rejects"] / m, "learned": rb["stats"]["rejects"] / m},
            "counts": {"plain": counts(ra), "learned": counts(rb)},
            "counts_equal": counts(ra) == counts(rb), "endpoint_agreement_1e-10": agree,
+           "launch_shape": {"team_warps": team, "iters_per_launch": iters,
+                            "tuned_on_paths": case["tune_paths"]},
            "train": {"systems": len(case["train_seeds"]), "paths_each": train_paths, "precision": "D",
                      "samples": int(sum(f.shape[0] for f in feats)), "first_loss": float(losses[0]),
                      "last_loss": float(losses[-1]), "seconds": train_s}}

@@ -362,6 +362,20 @@ int ht_track_paths_ex(ht_system* f, const int32_t* start_deg, const double* gamm
                       double* t_end, int32_t* steps, ht_stats* stats, const ht_track_io* io, void* stream);
 
 /*
+ * ht_tune_track -- autotuner for ht_track_paths on this system: tracks the
+ * first n_paths paths (from the start solutions) once per candidate launch
+ * shape -- team_warps in {1, 2, 4, 8} (up to n) and iters_per_launch in
+ * {2, 4, 8}, p's other settings unchanged (p may be NULL: defaults) -- keeps
+ * the fastest (wall time of the call) in the system, where it replaces the
+ * built-in choice whenever a call's params leave team_warps or
+ * iters_per_launch at 0, and reports it (output pointers may be NULL).  The
+ * launch shape changes the speed only: every team size and launch shape gives
+ * the same results.  Allocates its own output buffers.  Blocks.
+ */
+int ht_tune_track(ht_system* f, const int32_t* start_deg, const double* gamma, int64_t n_paths, const ht_params* p,
+                  int* team_warps, int* iters_per_launch, double* best_ms, void* stream);
+
+/*
  * ht_step_labels -- training labels for the learned step: every record is
  * restarted once per multiplier mu_j (mults host [n_mult], n_mult <= 64) with
  * its step h scaled by mu_j, and takes one step of at most newton_max

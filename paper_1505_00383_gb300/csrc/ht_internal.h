@@ -15,6 +15,8 @@ struct ht_system {
   int max_k = 0, max_exp = 0, max_deg = 0;
   int eval_variant = -1;         // 0 unrolled, 1 compact FP64 bodies, 2 integer limbs, -1 default
   int eval_threads = 0;          // CTA size of the evaluation kernel, 0 = default (128)
+  int track_team = 0;            // tuned tracker team size and rounds per launch (0: defaults)
+  int track_iters = 0;
   std::vector<int32_t> n_terms;  // host copies
   std::vector<int8_t> exps;
   std::vector<double> coef;

@@ -343,7 +343,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
 
   // Rounds: [track (iters Newton steps) ; compact] x rounds_per_sync per host
   // read of the active count, captured once per team size as a CUDA graph.
-  const int iters = P.iters_per_launch > 0 ? P.iters_per_launch : 4;
+  const int iters = P.iters_per_launch > 0 ? P.iters_per_launch : (s->track_iters > 0 ? s->track_iters : 4);
   const int rounds = P.rounds_per_sync > 0 ? P.rounds_per_sync : 8;
   // Team size: the largest power of two up to 8 warps and n.  More warps per
   // group means fewer groups in flight for the same FP64 issue rate, so the
@@ -353,6 +353,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   auto pick_team = [&](int64_t active) {
     (void)active;
     if (P.team_warps > 0) return P.team_warps;
+    if (s->track_team > 0 && s->track_team <= 8) return s->track_team;
     int t = 1;
     while (t < 8 && 2 * t <= n) t *= 2;
     return t;
@@ -445,6 +446,59 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
 }  // extern "C"
 
 extern "C" {
+
+int ht_tune_track(ht_system* s, const int32_t* start_deg, const double* gamma, int64_t n_paths, const ht_params* p,
+                  int* team_warps, int* iters_per_launch, double* best_ms, void* stream) {
+  clear_error();
+  if (!s || n_paths < 1 || n_paths > 0x7fffffff) return set_error(HT_EINVAL, "ht_tune_track: bad arguments");
+  const int n = s->nv, L = s->limbs;
+  ht_params P;
+  if (p)
+    P = *p;
+  else
+    ht_default_params(L, &P);
+  const size_t bx = (size_t)n * 2 * L * n_paths * sizeof(double), bt = (size_t)n_paths * sizeof(double);
+  char* buf = nullptr;
+  cudaError_t e = cudaMalloc((void**)&buf, bx + bt + (size_t)n_paths + 512);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return set_error(HT_ENOMEM, "ht_tune_track: output buffers");
+  }
+  double* x = (double*)buf;
+  double* t = (double*)(buf + bx);
+  int8_t* st = (int8_t*)(buf + bx + bt);
+  const int saved_team = s->track_team, saved_iters = s->track_iters;
+  double best = 1e300;
+  int bt_team = 0, bt_iters = 0, rc = HT_OK;
+  const int teams[4] = {1, 2, 4, 8}, its[3] = {2, 4, 8};
+  for (int a = 0; a < 4 && rc == HT_OK; ++a) {
+    if (teams[a] > 1 && teams[a] > n) continue;
+    for (int b = 0; b < 3 && rc == HT_OK; ++b) {
+      ht_params Q = P;
+      Q.team_warps = teams[a];
+      Q.iters_per_launch = its[b];
+      ht_stats stats;
+      rc = ht_track_paths_ex(s, start_deg, gamma, n_paths, 0, nullptr, &Q, x, st, t, nullptr, &stats, nullptr, stream);
+      if (rc == HT_OK && stats.ms < best) {
+        best = stats.ms;
+        bt_team = teams[a];
+        bt_iters = its[b];
+      }
+    }
+  }
+  cudaFree(buf);
+  if (rc != HT_OK) {
+    s->track_team = saved_team;
+    s->track_iters = saved_iters;
+    return rc;
+  }
+  s->track_team = bt_team;
+  s->track_iters = bt_iters;
+  if (team_warps) *team_warps = bt_team;
+  if (iters_per_launch) *iters_per_launch = bt_iters;
+  if (best_ms) *best_ms = best;
+  return HT_OK;
+}
 
 int ht_track_paths(ht_system* s, const int32_t* start_deg, const double* gamma, int64_t n_paths, int64_t first_path,
                    const double* x0, const ht_params* p, double* x_end, int8_t* status, double* t_end, int32_t* steps,

@@ -48,6 +48,8 @@ SIGNATURES = {
     "ht_compact_noalloc": ([P, I64, P, P, P], I32),
     "ht_track_paths": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P], I32),
     "ht_track_paths_ex": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P, P], I32),
+    "ht_tune_track": ([P, P, P, I64, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(ctypes.c_double), P], I32),
     "ht_record_size": ([I32, I32, I32], I64),
     "ht_step_labels": ([P, P, P, P, I64, P, I32, P, I32, P, P], I32),
     "ht_step_features": ([I32, I32, I32, I32, I64, P, P, P], I32),
@@ -348,6 +350,19 @@ def ht_track_paths_ex(sys: System, start_deg, gamma, n_paths, first_path, x0, pa
     ip = None if io is None else ctypes.byref(io)
     _check(lib().ht_track_paths_ex(sys.handle, _ptr(d), _ptr(g), n_paths, first_path, _ptr(x0), pp, _ptr(x_end),
                                    _ptr(status), _ptr(t_end), _ptr(steps), sp, ip, _stream(stream)))
+
+
+def ht_tune_track(sys: System, start_deg, gamma, n_paths, params=None, stream=None):
+    """Returns (team_warps, iters_per_launch, ms) of the fastest launch shape,
+    which the system then uses by default."""
+    import numpy as np
+    d = np.ascontiguousarray(start_deg, dtype=np.int32)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    team, iters, ms = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+    pp = None if params is None else ctypes.byref(params)
+    _check(lib().ht_tune_track(sys.handle, _ptr(d), _ptr(g), n_paths, pp, ctypes.byref(team), ctypes.byref(iters),
+                               ctypes.byref(ms), _stream(stream)))
+    return team.value, iters.value, ms.value
 
 
 def ht_step_labels(sys: System, start_deg, gamma, params, n_rec, records, mults, newton_max, labels,

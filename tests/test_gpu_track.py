@@ -331,3 +331,26 @@ def test_endpoint_check_rejects_bad_arguments(ht):
     with pytest.raises(ht.HTError):  # no polish rounds
         ht.ht_track_paths_ex(hs, [2] * 6, (1.0, 0.0), m, 0, x1, ht.ht_default_params(2, polish_max=0), x, st, t, None,
                              None, ht.ht_track_io(polish_only=1, x0_limbs=1))
+
+
+def test_track_autotuner_picks_a_valid_shape_and_keeps_results(ht):
+    """ht_tune_track times every launch shape on a path sample and keeps the
+    fastest in the system; tracking with the tuned defaults gives the same
+    bits as any explicit shape."""
+    s = synth.config_system("c0_plain_d")
+    gam = synth.random_gamma(0)
+    hs = ht.system_from(s, 1)
+    p = ht.ht_default_params(1, h_min=1e-9)
+    team, iters, ms = ht.ht_tune_track(hs, s.degrees(), gam, 64, p)
+    assert team in (1, 2, 4) and iters in (2, 4, 8) and ms > 0
+    m = 64
+    out = []
+    for tw, it in ((0, 0), (2, 4)):
+        x = torch.full((s.n_vars, 2, 1, m), np.nan, dtype=torch.float64, device="cuda")
+        st = torch.full((m,), 9, dtype=torch.int8, device="cuda")
+        t = torch.full((m,), np.nan, dtype=torch.float64, device="cuda")
+        ht.ht_track_paths(hs, s.degrees(), gam, m, 0, None, ht.ht_default_params(1, h_min=1e-9, team_warps=tw,
+                                                                                 iters_per_launch=it), x, st, t)
+        torch.cuda.synchronize()
+        out.append((x.cpu().numpy(), st.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0], equal_nan=True) and np.array_equal(out[0][1], out[1][1])
