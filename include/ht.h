@@ -314,9 +314,12 @@ int ht_track_paths(ht_system* f, const int32_t* start_deg, const double* gamma, 
  *   Learned step sizes.  With mlp != NULL, at the start of each step the
  *   network maps the step features (ht_step_features) to rho; the step tried
  *   is clamp(h exp(clamp(rho, rho_min, rho_max)), h_min, h_max) in place of
- *   the plain rule's h.  The corrector still judges the step: a rejected
- *   learned step shrinks as usual and the next fallback_steps steps of that
- *   path use the plain rule.
+ *   the plain rule's h.  With alpha_max > 0 the second output is a tangent
+ *   correction: the learned step's predicted point is x + (1 + alpha)(p - x)
+ *   with p the extrapolation predictor's point, x the current point and
+ *   alpha = clamp(output, -alpha_max, alpha_max).  The corrector still judges
+ *   the step: a rejected learned step shrinks as usual and the next
+ *   fallback_steps steps of that path use the plain rule.
  *
  *   Start points of another precision.  x0_limbs (1, 2 or 4, at most the
  *   system's L; 0 means L) is the number of limbs per component of x0, laid
@@ -355,6 +358,7 @@ typedef struct ht_track_io {
   double* last_dx_out;   /* device [n_paths] or NULL */
   double* last_res_out;  /* device [n_paths] or NULL */
   int32_t* newton_out;   /* device [n_paths] or NULL */
+  double alpha_max;      /* learned tangent correction clamp in [0, 1] (0: off) */
 } ht_track_io;
 
 int ht_track_paths_ex(ht_system* f, const int32_t* start_deg, const double* gamma, int64_t n_paths,
@@ -382,7 +386,11 @@ int ht_tune_track(ht_system* f, const int32_t* start_deg, const double* gamma, i
  * evaluate-correct rounds (p's other settings apply; h_min is lifted).  Among
  * the accepted probes the label takes the one with the most progress per
  * round, mu_j / rounds_j (ties to the larger mu_j): rho = log mu_j (log of the
- * smallest mu_j if no probe was accepted), and 0 for the second output.
+ * smallest mu_j if no probe was accepted); the second output is that probe's
+ * tangent correction alpha = Re <p - x, x* - p> / |p - x|^2 (x the record's
+ * point, p the extrapolation predictor's point at the probe's t1, x* the
+ * probe's corrected point; leading limbs, clamped to [-1, 1]; 0 without an
+ * accepted probe or when p = x).
  *   records device [n_rec][R]; labels device [n_rec][2] floats.  Blocks.
  */
 int ht_step_labels(ht_system* f, const int32_t* start_deg, const double* gamma, const ht_params* p, int64_t n_rec,

@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(32) mgs_kernel(double* A, double* R, double* x
 // network's registers do not weigh on the Newton rounds' allocation.
 template <int L>
 __device__ __noinline__ double learned_step(const TrackArgs& a, MlpWarpSmem& stage, bool want, int64_t p, double t,
-                                            double h, int nh, int cap) {
+                                            double h, int nh, int cap, double* alpha) {
   float f[FEAT];
   if (want)
     step_features<L>(f, t, h, nh, cap, a.n, a.ht + p, a.m, a.hx + p, a.m, a.last_dx[p], a.last_res[p],
@@ -344,9 +344,11 @@ __device__ __noinline__ double learned_step(const TrackArgs& a, MlpWarpSmem& sta
   float y[2];
   mlp_forward_warp(*static_cast<const MlpSmem*>(a.mlp_img), stage, f, y);
   double hs = h;
+  *alpha = 0.0;
   if (want) {
     const double rho = fmin(a.rho_max, fmax(a.rho_min, (double)y[0]));
     hs = fmin(a.prm.h_max, fmax(a.prm.h_min, h * exp(rho)));
+    if (a.alpha_max > 0.0) *alpha = fmin(a.alpha_max, fmax(-a.alpha_max, (double)y[1]));
   }
   return hs;
 }
@@ -375,6 +377,7 @@ template <int L, bool LEARN, bool INT>
 __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kernel(TrackArgs a) {
   __shared__ double red[4][8][32];  // per-warp partials: residual, update, point norms; finiteness
   __shared__ double sh_h[32];       // learned step of each lane's path
+  __shared__ double sh_alpha[32];   // learned tangent correction of each lane's path
   __shared__ long long sh_slot[32]; // trace record slot of each lane's path (-1: none)
   // The network's weights are read from the device image (L1/L2): staging
   // them in shared memory would enlarge the shared-memory carveout and take
@@ -410,6 +413,7 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
       double t = act ? a.t[p] : 0.0, h = act ? a.h[p] : 0.0, t1 = act ? a.t1[p] : 0.0;
       int nh = act ? a.nh[p] : 1;
       int fb = act ? a.fallback[p] : 0;
+      double alpha = 0.0;  // tangent correction of a learned step (0: the plain predictor)
       const bool start = act && ph == PH_TRACK && it == 0;
       // ---- A0: record the step start, propose a learned step
       if (a.trace) {
@@ -449,10 +453,11 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
         // warp 0 runs the network only in rounds where one of its paths
         // starts a learned step (about one round in three)
         if (warp == 0 && __any_sync(0xffffffffu, start && fb == 0))
-          sh_h[lane] = learned_step<L>(a, mlp_stage, start && fb == 0, p, t, h, nh, cap);
+          sh_h[lane] = learned_step<L>(a, mlp_stage, start && fb == 0, p, t, h, nh, cap, &sh_alpha[lane]);
         __syncthreads();
         if (start && fb == 0) {
           h = sh_h[lane];
+          alpha = sh_alpha[lane];
           fb = -1;  // this step is a learned one
         }
       }
@@ -478,6 +483,10 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
           cx<L> acc = czero<L>();
           for (int j = 0; j < mm; ++j)
             acc = cadd(acc, cscale_r(ld<L>(a.hx, (int64_t)(base + j) * n + i, m, p), w[j]));
+          if (alpha != 0.0) {  // learned tangent correction: x + (1 + alpha)(pred - x)
+            const cx<L> xc = ld<L>(a.hx, (int64_t)(nh - 1) * n + i, m, p);
+            acc = cadd(xc, cscale_r(csub(acc, xc), r_from<L>(1.0 + alpha)));
+          }
           st<L>(a.xp, i, m, p, acc);
         }
       } else if (act && ph == PH_POLISH) {

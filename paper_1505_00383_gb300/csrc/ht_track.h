@@ -80,6 +80,7 @@ struct TrackArgs {
   const void* mlp_img;     // network image (MlpSmem layout, device memory); nullptr: plain rule
   int fallback_steps;
   double rho_min, rho_max;
+  double alpha_max;        // learned tangent correction clamp (0: off)
 };
 
 template <int L>

@@ -64,16 +64,28 @@ __global__ void probe_records_kernel(const double* __restrict__ rec, int64_t n_r
   }
 }
 
-// Label of record r: among the multipliers whose single probe step was
-// accepted (t moved past the record's t), the one with the most progress per
-// Newton round, mu_j / rounds_j (ties to the larger mu_j); rho = its log, or
-// the log of the smallest multiplier if no probe was accepted.
-__global__ void labels_kernel(const double* __restrict__ rec, int64_t n_rec, int64_t R, int n_mult,
-                              const double* __restrict__ mults, const double* __restrict__ t_end,
-                              const int32_t* __restrict__ rounds, float* __restrict__ labels) {
+// Label of record r:
+//   rho   among the multipliers whose single probe step was accepted (t
+//         moved past the record's t), the one with the most progress per
+//         Newton round, mu_j / rounds_j (ties to the larger mu_j); rho = its
+//         log, or the log of the smallest multiplier if no probe was accepted;
+//   alpha for that accepted probe, the scale of the predictor's displacement
+//         that best reaches the corrected point: with x the record's current
+//         point, p the extrapolation predictor's point at the probe's t1 and
+//         x* the probe's corrected point, alpha = Re <p - x, x* - p> / |p - x|^2
+//         over all coordinates (leading limbs), clamped to [-1, 1]; 0 if no
+//         probe was accepted or p = x.
+// px is the probes' end points [n][2][L][n_rec n_mult].
+__global__ void labels_kernel(const double* __restrict__ rec, int64_t n_rec, int64_t R, int n, int L, int cap,
+                              int n_mult, const double* __restrict__ mults, const double* __restrict__ t_end,
+                              const int32_t* __restrict__ rounds, const double* __restrict__ px,
+                              float* __restrict__ labels) {
+  const int64_t P = n_rec * n_mult;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n_rec; r += (int64_t)gridDim.x * blockDim.x) {
-    const double t0 = rec[r * R + 1];
+    const double* h = rec + r * R;
+    const double t0 = h[1];
     double best = -1.0, best_eff = -1.0, lo = mults[0];
+    int jb = -1;
     for (int j = 0; j < n_mult; ++j) {
       lo = fmin(lo, mults[j]);
       if (t_end[r * n_mult + j] > t0) {
@@ -82,11 +94,48 @@ __global__ void labels_kernel(const double* __restrict__ rec, int64_t n_rec, int
         if (eff > best_eff || (eff == best_eff && mults[j] > best)) {
           best_eff = eff;
           best = mults[j];
+          jb = j;
         }
       }
     }
+    double alpha = 0.0;
+    if (jb >= 0) {
+      // the predictor of the tracker at t1 (Lagrange form over the history)
+      int nh = (int)h[3];
+      nh = nh < 1 ? 1 : (nh > cap ? cap : nh);
+      const double step = fmin(h[2] * mults[jb], 1.0 - t0);
+      const double t1 = (step >= 1.0 - t0) ? 1.0 : t0 + step;
+      const int mm = nh < cap ? nh : cap, base = nh - mm;
+      double w[8];
+      for (int j = 0; j < mm; ++j) {
+        double num = 1.0, den = 1.0;
+        for (int i = 0; i < mm; ++i) {
+          if (i == j) continue;
+          num *= t1 - h[REC_HDR + base + i];
+          den *= h[REC_HDR + base + j] - h[REC_HDR + base + i];
+        }
+        w[j] = num / den;
+      }
+      const double* hx = h + REC_HDR + cap;  // [cap][n][2][L]
+      const int64_t q = r * n_mult + jb;
+      double dot = 0.0, nrm = 0.0;
+      for (int i = 0; i < n; ++i) {
+        double pre = 0.0, pim = 0.0;
+        for (int j = 0; j < mm; ++j) {
+          pre += w[j] * hx[(((int64_t)(base + j) * n + i) * 2 + 0) * L];
+          pim += w[j] * hx[(((int64_t)(base + j) * n + i) * 2 + 1) * L];
+        }
+        const double xre = hx[(((int64_t)(nh - 1) * n + i) * 2 + 0) * L];
+        const double xim = hx[(((int64_t)(nh - 1) * n + i) * 2 + 1) * L];
+        const double sre = px[((int64_t)(i * 2 + 0) * L) * P + q], sim = px[((int64_t)(i * 2 + 1) * L) * P + q];
+        const double dre = pre - xre, dim = pim - xim;
+        dot += dre * (sre - pre) + dim * (sim - pim);
+        nrm += dre * dre + dim * dim;
+      }
+      alpha = nrm > 0.0 ? fmin(1.0, fmax(-1.0, dot / nrm)) : 0.0;
+    }
     labels[r * 2 + 0] = (float)log(best > 0.0 ? best : lo);
-    labels[r * 2 + 1] = 0.0f;
+    labels[r * 2 + 1] = (float)alpha;
   }
 }
 
@@ -226,7 +275,8 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
     return set_error(HT_EINVAL, "ht_track_paths_ex: trace needs a device buffer, a device counter and stride >= 1");
   if (IO.init_records && !is_device_ptr(IO.init_records))
     return set_error(HT_EINVAL, "ht_track_paths_ex: init_records must be device memory");
-  if (IO.mlp && (IO.fallback_steps < 0 || IO.fallback_steps > 100 || !(IO.rho_max >= IO.rho_min)))
+  if (IO.mlp && (IO.fallback_steps < 0 || IO.fallback_steps > 100 || !(IO.rho_max >= IO.rho_min) ||
+                 !(IO.alpha_max >= 0.0 && IO.alpha_max <= 1.0)))
     return set_error(HT_EINVAL, "ht_track_paths_ex: invalid learned-step settings");
   const int x0_limbs = IO.x0_limbs > 0 ? IO.x0_limbs : L;
   if (IO.x0_limbs < 0 || x0_limbs > L || (x0_limbs == 3))
@@ -316,6 +366,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.fallback_steps = IO.fallback_steps;
   a.rho_min = IO.rho_min;
   a.rho_max = IO.rho_max;
+  a.alpha_max = IO.mlp ? IO.alpha_max : 0.0;
   a.x0 = IO.init_records ? nullptr : x0;
   a.x0_limbs = x0_limbs;
   a.polish_only = IO.polish_only ? 1 : 0;
@@ -553,7 +604,7 @@ int ht_step_labels(ht_system* s, const int32_t* start_deg, const double* gamma, 
     rc = ht_track_paths_ex(s, start_deg, gamma, P, 0, nullptr, &pp, px, pst, pt, nullptr, nullptr, &io, stream);
   }
   if (rc == HT_OK) {
-    labels_kernel<<<256, 256, 0, st>>>(records, n_rec, R, n_mult, pm, pt, pk, labels);
+    labels_kernel<<<256, 256, 0, st>>>(records, n_rec, R, n, L, prm->max_order + 1, n_mult, pm, pt, pk, px, labels);
     e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) rc = cuda_fail(e, "ht_step_labels");
   }

@@ -71,7 +71,7 @@ class ht_track_io(ctypes.Structure):
                 ("trace_count", ctypes.c_void_p), ("trace_stride", ctypes.c_int32), ("fallback_steps", ctypes.c_int32),
                 ("mlp", ctypes.c_void_p), ("rho_min", ctypes.c_double), ("rho_max", ctypes.c_double),
                 ("x0_limbs", ctypes.c_int32), ("polish_only", ctypes.c_int32), ("last_dx_out", ctypes.c_void_p),
-                ("last_res_out", ctypes.c_void_p), ("newton_out", ctypes.c_void_p)]
+                ("last_res_out", ctypes.c_void_p), ("newton_out", ctypes.c_void_p), ("alpha_max", ctypes.c_double)]
 
 
 class ht_stats(ctypes.Structure):

@@ -107,7 +107,7 @@ def train(feat, lab, epochs=30, batch=4096, lr=2e-3, seed=1):
 
 
 def track(system, limbs, gamma, n_paths, params, net=None, fallback_steps=1, first_path=0, check_limbs=0,
-          check_params=None):
+          check_params=None, alpha_max=0.0):
     """ht_track_paths_ex with (net given) or without the learned step; returns
     host arrays and stats.  With check_limbs > limbs the endpoints are then
     checked in that precision: Newton's method on the target system from
@@ -122,7 +122,8 @@ def track(system, limbs, gamma, n_paths, params, net=None, fallback_steps=1, fir
     stats = ht.ht_stats()
     io = None
     if net is not None:
-        io = ht.ht_track_io(mlp=net.handle, fallback_steps=fallback_steps, rho_min=RHO_RANGE[0], rho_max=RHO_RANGE[1])
+        io = ht.ht_track_io(mlp=net.handle, fallback_steps=fallback_steps, rho_min=RHO_RANGE[0], rho_max=RHO_RANGE[1],
+                            alpha_max=alpha_max)
     ht.ht_track_paths_ex(hs, system.degrees(), gamma, n_paths, first_path, None, params, x, st, t, None, stats, io)
     out = dict(stats=stats.as_dict())
     if check_limbs > limbs:

@@ -164,8 +164,10 @@ def test_features_follow_their_definition(ht):
 def test_labels_follow_their_definition(ht):
     """Each record is probed once per multiplier (one step, the tracker's
     round limit); the label is the log of the accepted multiplier with the
-    most progress per Newton round, ties to the larger; the smallest if none
-    was accepted.  Probes re-run here one multiplier at a time."""
+    most progress per Newton round, ties to the larger (the smallest if none
+    was accepted), and the tangent correction toward that probe's corrected
+    point.  Probes re-run here one multiplier at a time; the predictor is
+    re-derived from the record in numpy."""
     from paper_1505_00383_gb300 import learned
     s = synth.config_system("c0_plain_d")
     gam = synth.random_gamma(0)
@@ -178,6 +180,7 @@ def test_labels_follow_their_definition(ht):
     t0 = rec[:, 1].cpu().numpy()
     acc = np.zeros((n_rec, len(learned.MULTS)), bool)
     rounds = np.zeros((n_rec, len(learned.MULTS)), np.int64)
+    ends = np.zeros((n_rec, len(learned.MULTS), s.n_vars), complex)
     hs = ht.system_from(s, 1)
     pp = ht.ht_default_params(1, h_min=1e-300, max_steps=1, polish_max=0)
     for j, mu in enumerate(learned.MULTS):
@@ -192,14 +195,39 @@ def test_labels_follow_their_definition(ht):
         torch.cuda.synchronize()
         acc[:, j] = t.cpu().numpy() > t0
         rounds[:, j] = k.cpu().numpy()
+        xe = x.cpu().numpy()
+        ends[:, j] = (xe[:, 0, 0, :] + 1j * xe[:, 1, 0, :]).T
     assert acc.any() and (~acc).any() and np.all(rounds >= 1) and np.all(rounds <= prm.newton_max)
+    recs = rec.cpu().numpy()
+    cap, n = prm.max_order + 1, s.n_vars
+    n_alpha = 0
     for q in range(n_rec):
-        best, eff = None, -1.0
+        best, eff, jb = None, -1.0, -1
         for j, mu in enumerate(learned.MULTS):
             if acc[q, j] and (mu / rounds[q, j] > eff or (mu / rounds[q, j] == eff and mu > best)):
-                best, eff = mu, mu / rounds[q, j]
+                best, eff, jb = mu, mu / rounds[q, j], j
         want = np.float32(np.log(best if best is not None else min(learned.MULTS)))
-        assert lab[q, 0] == want and lab[q, 1] == 0.0, (q, lab[q], want, acc[q], rounds[q])
+        assert lab[q, 0] == want, (q, lab[q], want, acc[q], rounds[q])
+        alpha = 0.0
+        if jb >= 0:  # tangent correction toward the chosen probe's corrected point
+            r = recs[q]
+            t, h, nh = r[1], r[2], int(r[3])
+            tv = r[16:16 + cap]
+            hx = r[16 + cap:].reshape(cap, n, 2)
+            step = min(h * best, 1.0 - t)
+            t1 = 1.0 if step >= 1.0 - t else t + step
+            mm = min(nh, cap)
+            base = nh - mm
+            w = [np.prod([(t1 - tv[base + i]) / (tv[base + j] - tv[base + i]) for i in range(mm) if i != j])
+                 for j in range(mm)]
+            pred = sum(w[j] * (hx[base + j, :, 0] + 1j * hx[base + j, :, 1]) for j in range(mm))
+            xc = hx[nh - 1, :, 0] + 1j * hx[nh - 1, :, 1]
+            d = pred - xc
+            nrm = np.sum(np.abs(d) ** 2)
+            alpha = float(np.clip(np.sum((np.conj(d) * (ends[q, jb] - pred)).real) / nrm, -1, 1)) if nrm > 0 else 0.0
+            n_alpha += alpha != 0.0
+        assert abs(lab[q, 1] - alpha) <= 1e-5 + 1e-4 * abs(alpha), (q, lab[q, 1], alpha)
+    assert n_alpha > 0
 
 
 def test_trained_network_gains_over_the_plain_rule(ht):
