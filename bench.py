@@ -168,6 +168,26 @@ def _kernel_sha():
     return h.hexdigest()[:16]
 
 
+# bounded oracle samples of the tracking workloads (first paths of the system
+# the GPU tracks; about 5-15 s each on the host cores)
+ORACLE_TRACK_SAMPLE = {"c0_plain_d": 64, "c2_batched_dd": 32, "c3_learned_d": 2048, "c4_stress_qd": 8}
+
+
+def oracle_track_rate(name, seed, limbs, h_min, sample):
+    """The oracle tracker (plain rule, all host cores) on the first `sample`
+    paths of the workload's system: paths/s and the cores used."""
+    import oracle
+    oracle.build()
+    s = synth.config_system(name, seed)
+    g = synth.random_gamma(seed)
+    P = oracle.default_params(limbs, h_min=h_min)
+    t0 = time.perf_counter()
+    oracle.track(s, s.degrees(), g, np.arange(sample), limbs, P, n_threads=0)
+    sec = time.perf_counter() - t0
+    return {"value": sample / sec, "unit": "paths/s", "cores": os.cpu_count() or 1, "kind": "oracle",
+            "sample": "first %d paths, plain rule" % sample}
+
+
 def cpu_oracle_rate(system, budget_pts, threads=0, seed=77):
     """Oracle throughput in the metric's unit on a bounded sample: for each
     precision, budget_pts[L] points evaluated by the oracle's reverse mode."""
@@ -483,12 +503,21 @@ def run_ours(a):
         peaks["hbm_GBps_measured"] = json.load(open(mp)).get("hbm_gbs")
 
     tracking = {}
+    oracle_side = rank == 0 and world == 1 and not a.no_cpu
     for name in [w for w in a.track.split(",") if w]:
         tracking[name] = track_workload(ht, torch, name, rank, world)
-    if a.learned > 0:
-        tracking["c3_learned_vs_plain"] = learned_vs_plain(ht, torch, world, "c3_learned_d", a.learned)
-    if a.stress > 0:
-        tracking["c4_learned_vs_plain"] = learned_vs_plain(ht, torch, world, "c4_stress_qd", a.stress)
+        if oracle_side:
+            cfg = synth.CONFIGS[name]
+            tracking[name]["cpu_baseline"] = oracle_track_rate(name, cfg["seed"], TRACK_LIMBS[name],
+                                                               0.01 if name == "c0_plain_d" else 1e-6,
+                                                               ORACLE_TRACK_SAMPLE[name])
+    for name, m, key in (("c3_learned_d", a.learned, "c3_learned_vs_plain"),
+                         ("c4_stress_qd", a.stress, "c4_learned_vs_plain")):
+        if m > 0:
+            tracking[key] = learned_vs_plain(ht, torch, world, name, m)
+            if oracle_side:
+                tracking[key]["cpu_baseline"] = oracle_track_rate(name, LEARNED_CASES[name]["eval_seed"],
+                                                                  TRACK_LIMBS[name], 1e-9, ORACLE_TRACK_SAMPLE[name])
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:

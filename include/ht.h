@@ -100,9 +100,12 @@ int ht_eval_diff(const ht_system* sys, int64_t n_pts, const double* x, double* v
 /*
  * ht_eval_diff_host -- ht_eval_diff on HOST buffers of the same layouts: copies
  * x to the device, evaluates, copies val and jac back, and returns when the
- * results are in host memory.  Uses a device workspace owned by the system
- * (grown on demand, freed with the system).  Pinned host memory gives the
- * fastest copies; pageable memory works.
+ * results are in host memory.  From 8,192 points on, the points go in 2 or 8
+ * column blocks over two internal streams (after the work already queued on
+ * `stream`), so copies of one block overlap the evaluation of the next.
+ * Uses a device workspace and two streams owned by the system (grown on
+ * demand, freed with the system).  Pinned host memory gives the fastest
+ * copies; pageable memory works.
  */
 int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, double* val_host,
                       double* jac_host, void* stream);

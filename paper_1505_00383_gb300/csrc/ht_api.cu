@@ -197,6 +197,8 @@ int ht_destroy_system(ht_system* s) {
   if (s->d_track_ws) cudaFree(s->d_track_ws);
   if (s->d_coef_fz) cudaFree(s->d_coef_fz);
   if (s->h_count) cudaFreeHost(s->h_count);
+  for (auto& hs : s->host_streams)
+    if (hs) cudaStreamDestroy(hs);
   for (auto& g : s->graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   delete s;
@@ -246,14 +248,20 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
   int rc = check_eval_args(s, n_pts, x_host, val_host, jac_host, false);
   if (rc != HT_OK || n_pts == 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
+  // Pipelined in chunks of points: two streams each copy a chunk in,
+  // evaluate it and copy it out, so one chunk's copies overlap the other's
+  // evaluation.  A chunk is a column block of the point-fastest layouts: one
+  // 2-D copy per array (rows = entries, row length = the chunk's points).
   const size_t L = s->limbs;
-  size_t bx = (size_t)s->nv * 2 * L * n_pts * 8;
-  size_t bv = (size_t)s->np * 2 * L * n_pts * 8;
-  size_t bj = (size_t)s->np * s->nv * 2 * L * n_pts * 8;
-  size_t need = bx + bv + bj;
+  const int64_t rx = (int64_t)s->nv * 2 * L, rv = (int64_t)s->np * 2 * L, rj = (int64_t)s->np * s->nv * 2 * L;
+  const int n_chunks = n_pts >= 8 * 4096 ? 8 : (n_pts >= 2 * 4096 ? 2 : 1);
+  const int64_t C = ((n_pts + n_chunks - 1) / n_chunks + 31) / 32 * 32;
+  const int slots = n_chunks > 1 ? 2 : 1;
+  const size_t per_slot = (size_t)(rx + rv + rj) * C * 8;
+  const size_t need = per_slot * slots;
   if (s->ws_bytes < need) {
     if (s->d_ws) {
-      cudaStreamSynchronize(st);
+      cudaDeviceSynchronize();
       cudaFree(s->d_ws);
       s->d_ws = nullptr;
       s->ws_bytes = 0;
@@ -265,17 +273,52 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
     }
     s->ws_bytes = need;
   }
-  double* dx = (double*)s->d_ws;
-  double* dv = (double*)((char*)s->d_ws + bx);
-  double* dj = (double*)((char*)s->d_ws + bx + bv);
-  cudaError_t e = cudaMemcpyAsync(dx, x_host, bx, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copy in");
-  rc = launch_evaldiff(s, n_pts, dx, dv, dj, st);
+  for (int k = 0; k < 2 && slots > 1; ++k)
+    if (!s->host_streams[k]) {
+      cudaError_t e = cudaStreamCreateWithFlags(&s->host_streams[k], cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: stream");
+    }
+  cudaStream_t sts[2] = {st, st};
+  cudaEvent_t ready = nullptr;
+  if (slots > 1) {
+    sts[0] = s->host_streams[0];
+    sts[1] = s->host_streams[1];
+    cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, st);  // after the caller's earlier work
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sts[0], ready, 0);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sts[1], ready, 0);
+    if (e != cudaSuccess) {
+      if (ready) cudaEventDestroy(ready);
+      return cuda_fail(e, "ht_eval_diff_host: ordering");
+    }
+  }
+  cudaError_t e = cudaSuccess;
+  for (int c = 0; c < n_chunks && rc == HT_OK && e == cudaSuccess; ++c) {
+    const int64_t p0 = (int64_t)c * C;
+    if (p0 >= n_pts) break;
+    const int64_t cc = n_pts - p0 < C ? n_pts - p0 : C;
+    cudaStream_t cs = sts[c & 1];
+    char* slot = (char*)s->d_ws + per_slot * (c % slots);
+    double* dx = (double*)slot;
+    double* dv = dx + rx * cc;
+    double* dj = dv + rv * cc;
+    e = cudaMemcpy2DAsync(dx, cc * 8, x_host + p0, n_pts * 8, cc * 8, rx, cudaMemcpyHostToDevice, cs);
+    if (e != cudaSuccess) break;
+    rc = launch_evaldiff(s, cc, dx, dv, dj, cs);
+    if (rc != HT_OK) break;
+    e = cudaMemcpy2DAsync(val_host + p0, n_pts * 8, dv, cc * 8, cc * 8, rv, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(jac_host + p0, n_pts * 8, dj, cc * 8, cc * 8, rj, cudaMemcpyDeviceToHost, cs);
+  }
+  cudaError_t e2 = cudaStreamSynchronize(sts[0]);
+  if (slots > 1) {
+    cudaError_t e3 = cudaStreamSynchronize(sts[1]);
+    if (e2 == cudaSuccess) e2 = e3;
+    cudaEventDestroy(ready);
+  }
   if (rc != HT_OK) return rc;
-  e = cudaMemcpyAsync(val_host, dv, bv, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(jac_host, dj, bj, cudaMemcpyDeviceToHost, st);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copy out");
+  if (e == cudaSuccess) e = e2;
+  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copies");
   return HT_OK;
 }
 

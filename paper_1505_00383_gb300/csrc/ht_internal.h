@@ -31,6 +31,7 @@ struct ht_system {
   float* d_coef_lg = nullptr;    // [M] log2 |c| (-1000 for zero)
   void* d_ws = nullptr;          // workspace for the host-buffer entry points
   size_t ws_bytes = 0;
+  cudaStream_t host_streams[2] = {nullptr, nullptr};  // pipelined host-buffer evaluation
   void* d_track_ws = nullptr;    // per-path tracker state (grown on demand)
   size_t track_ws_bytes = 0;
   int32_t* h_count = nullptr;    // pinned host word: active paths after a round

@@ -112,10 +112,12 @@ def test_zero_points_is_a_noop_and_bad_args_are_rejected(ht):
         ht.ht_create_system(2, 1, [1], np.zeros((1, 2), np.int8), np.zeros((1, 2, 3)), 3)
 
 
-@pytest.mark.parametrize("L", [1, 4])
-def test_host_buffer_entry_point_matches(ht, L):
+@pytest.mark.parametrize("L,n", [(1, 70), (4, 70), (2, 2 * 4096 + 37), (1, 8 * 4096 + 5)])
+def test_host_buffer_entry_point_matches(ht, L, n):
+    """One block, two blocks and eight blocks with a ragged last block: the
+    pipelined host entry gives the device entry's bits."""
     s = synth.config_system("c2_batched_dd")
-    x = synth.unit_points(55, s.n_vars, 70, L)
+    x = synth.unit_points(55, s.n_vars, n, L)
     v1, j1 = _run(ht, s, x, L)
     v2, j2 = _run(ht, s, x, L, host=True)
     assert np.array_equal(v1, v2) and np.array_equal(j1, j2)
