@@ -234,7 +234,8 @@ def test_trained_network_gains_over_the_plain_rule(ht):
     """Train on step-start records of training systems (labels: the step
     each state allowed at the least cost per round), then track held-out systems: the learned step
     needs fewer Newton rounds than the plain rule, with the same endpoint set
-    and the same counts of converged, failed and diverged paths."""
+    and the same counts of converged, failed and diverged paths -- as the
+    plain GPU tracker, and on a sample of paths as the oracle's tracker."""
     from paper_1505_00383_gb300 import learned
     cfg = synth.CONFIGS["c3_learned_d"]
     prm = ht.ht_default_params(1, h_min=1e-9)
@@ -257,6 +258,13 @@ def test_trained_network_gains_over_the_plain_rule(ht):
             assert np.sum(a["status"] == code) == np.sum(b["status"] == code)
         ok, worst = match_sets(to_complex(a["x_end"])[a["status"] == 1], to_complex(b["x_end"])[b["status"] == 1],
                                1e-10)
+        assert ok, worst
+        # and against the oracle's plain tracker on the first 64 paths
+        o = oracle.track(s, s.degrees(), gam, np.arange(64), 1, oracle.default_params(1, h_min=1e-9))
+        for code in (1, -1, -2):
+            assert np.sum(o["status"] == code) == np.sum(b["status"][:64] == code)
+        ok, worst = match_sets(to_complex(o["x_end"])[o["status"] == 1],
+                               to_complex(b["x_end"][..., :64])[b["status"][:64] == 1], 1e-10)
         assert ok, worst
         tot_plain += a["stats"]["newton"]
         tot_learn += b["stats"]["newton"]
