@@ -90,36 +90,55 @@ __global__ void start_kernel(int n, const int32_t* __restrict__ deg, int64_t fir
 //   f0 t, f1 log10 h, f2 log10 |dx/dt|_inf / 4 (from the last two accepted
 //   points, 0 with fewer), f3 log10 |dx| of the last round / 16, f4 log10 |h|
 //   of the last round / 16, f5 rounds of the last step / newton_max, f6 last
-//   step rejected, f7 history length / cap, f8 log10(1 - t) / 16; each clamped
-//   to [-4, 4]; f9..f15 zero.
+//   step rejected, f7 history length / cap, f8 log10(1 - t) / 16,
+//   f9 log10 |d2x/dt2|_inf / 8 (twice the second divided difference of the
+//   last three accepted points, 0 with fewer), f10 log10(h / the last
+//   accepted step) / 2 (0 with fewer than two points); each clamped to
+//   [-4, 4]; f11..f15 zero.
 template <int L>
 __device__ __forceinline__ void step_features(float* f, double t, double h, int nh, int cap, int n,
                                               const double* tv, int64_t tstride, const double* hx, int64_t stride,
                                               double last_dx, double last_res, int last_its, int last_rej,
                                               int newton_max) {
-  double dxdt = 0.0;
+  double dxdt = 0.0, d2 = 0.0, hr = 0.0;
+  auto pt = [&](int s, int i, int c) { return hx[((((int64_t)s * n + i) * 2) * L + (int64_t)c * L) * stride]; };
+  auto tt = [&](int s) { return tv[(int64_t)s * tstride]; };
   if (nh >= 2) {
-    const double dt = tv[(int64_t)(nh - 1) * tstride] - tv[(int64_t)(nh - 2) * tstride];
+    const double dt = tt(nh - 1) - tt(nh - 2);
     double mx = 0.0;
     for (int i = 0; i < n; ++i) {
-      const int64_t q1 = (((int64_t)(nh - 1) * n + i) * 2) * L, q0 = (((int64_t)(nh - 2) * n + i) * 2) * L;
-      const double dr = hx[q1 * stride] - hx[q0 * stride];
-      const double di = hx[(q1 + L) * stride] - hx[(q0 + L) * stride];
+      const double dr = pt(nh - 1, i, 0) - pt(nh - 2, i, 0);
+      const double di = pt(nh - 1, i, 1) - pt(nh - 2, i, 1);
       mx = fmax(mx, sqrt(dr * dr + di * di));
     }
     dxdt = dt > 0.0 ? mx / dt : 0.0;
+    hr = dt > 0.0 ? log10(h / dt) / 2.0 : 0.0;
   }
-  double v[9] = {t,
-                 log10(h),
-                 log10(dxdt + 1e-30) / 4.0,
-                 log10(last_dx + 1e-300) / 16.0,
-                 log10(last_res + 1e-300) / 16.0,
-                 (double)last_its / (double)newton_max,
-                 (double)last_rej,
-                 (double)nh / (double)cap,
-                 log10(1.0 - t + 1e-16) / 16.0};
-  for (int i = 0; i < 9; ++i) f[i] = (float)fmin(4.0, fmax(-4.0, v[i]));
-  for (int i = 9; i < FEAT; ++i) f[i] = 0.0f;
+  if (nh >= 3) {
+    const double t2 = tt(nh - 1), t1 = tt(nh - 2), t0 = tt(nh - 3);
+    if (t2 > t1 && t1 > t0) {
+      double mx = 0.0;
+      for (int i = 0; i < n; ++i) {
+        const double ar = (pt(nh - 1, i, 0) - pt(nh - 2, i, 0)) / (t2 - t1) - (pt(nh - 2, i, 0) - pt(nh - 3, i, 0)) / (t1 - t0);
+        const double ai = (pt(nh - 1, i, 1) - pt(nh - 2, i, 1)) / (t2 - t1) - (pt(nh - 2, i, 1) - pt(nh - 3, i, 1)) / (t1 - t0);
+        mx = fmax(mx, sqrt(ar * ar + ai * ai));
+      }
+      d2 = 2.0 * mx / (t2 - t0);
+    }
+  }
+  double v[11] = {t,
+                  log10(h),
+                  log10(dxdt + 1e-30) / 4.0,
+                  log10(last_dx + 1e-300) / 16.0,
+                  log10(last_res + 1e-300) / 16.0,
+                  (double)last_its / (double)newton_max,
+                  (double)last_rej,
+                  (double)nh / (double)cap,
+                  log10(1.0 - t + 1e-16) / 16.0,
+                  nh >= 3 ? log10(d2 + 1e-30) / 8.0 : 0.0,
+                  hr};
+  for (int i = 0; i < 11; ++i) f[i] = (float)fmin(4.0, fmax(-4.0, v[i]));
+  for (int i = 11; i < FEAT; ++i) f[i] = 0.0f;
 }
 
 template <int L>

@@ -148,17 +148,21 @@ def test_features_follow_their_definition(ht):
         t, h, nh = r[k, 1], r[k, 2], int(r[k, 3])
         tv = r[k, 16:16 + cap]
         hx = r[k, 16 + cap:].reshape(cap, n, 2, 1)
+        xs = hx[:, :, 0, 0] + 1j * hx[:, :, 1, 0]
+        dxdt, f9, f10 = 0.0, 0.0, 0.0
         if nh >= 2:
-            d = hx[nh - 1, :, :, 0] - hx[nh - 2, :, :, 0]
-            dxdt = np.max(np.hypot(d[:, 0], d[:, 1])) / (tv[nh - 1] - tv[nh - 2])
-        else:
-            dxdt = 0.0
+            dt = tv[nh - 1] - tv[nh - 2]
+            dxdt = np.max(np.abs(xs[nh - 1] - xs[nh - 2])) / dt
+            f10 = np.log10(h / dt) / 2
+        if nh >= 3 and tv[nh - 1] > tv[nh - 2] > tv[nh - 3]:
+            a = (xs[nh - 1] - xs[nh - 2]) / (tv[nh - 1] - tv[nh - 2]) - (xs[nh - 2] - xs[nh - 3]) / (tv[nh - 2] - tv[nh - 3])
+            f9 = np.log10(2 * np.max(np.abs(a)) / (tv[nh - 1] - tv[nh - 3]) + 1e-30) / 8
         ref = [t, np.log10(h), np.log10(dxdt + 1e-30) / 4, np.log10(r[k, 4] + 1e-300) / 16,
                np.log10(r[k, 5] + 1e-300) / 16, r[k, 6] / prm.newton_max, r[k, 7], nh / cap,
-               np.log10(1 - t + 1e-16) / 16]
+               np.log10(1 - t + 1e-16) / 16, f9, f10]
         ref = np.clip(ref, -4, 4)
-        assert np.allclose(f[k, :9], ref, rtol=1e-5, atol=1e-6), (k, f[k, :9], ref)
-        assert np.all(f[k, 9:] == 0)
+        assert np.allclose(f[k, :11], ref, rtol=1e-5, atol=1e-5), (k, f[k, :11], ref)
+        assert np.all(f[k, 11:] == 0)
 
 
 def test_labels_follow_their_definition(ht):
