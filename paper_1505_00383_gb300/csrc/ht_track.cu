@@ -216,6 +216,43 @@ __global__ void init_kernel(TrackArgs a) {
 // [rows][cols + 1][2][L][m], R is [cols][cols + 1][2][L][m] (R[q][q] holds
 // 1 / r_qq), x is [cols][2][L][m].  Every thread of the CTA must call this
 // (it contains barriers); lanes with act == false only take the barriers.
+// The three accumulations of MGS.  In double each is a chain of fused
+// multiply-adds (4 FMAs for r + conj(a) b and for a - r q, 2 for s + |v|^2
+// against 6, 6 and 3 instructions through the complex helpers); in DD and QD
+// the helpers' fused two-term products.
+template <int L>
+__device__ __forceinline__ cx<L> acc_conj_mul(cx<L> r, const cx<L>& a, const cx<L>& b) {
+  if constexpr (L == 1) {
+    r.re = fma(a.re, b.re, r.re);
+    r.re = fma(a.im, b.im, r.re);
+    r.im = fma(a.re, b.im, r.im);
+    r.im = fma(-a.im, b.re, r.im);
+    return r;
+  } else {
+    return cadd(r, cconjmul(a, b));
+  }
+}
+template <int L>
+__device__ __forceinline__ cx<L> sub_mul(cx<L> a, const cx<L>& r, const cx<L>& q) {
+  if constexpr (L == 1) {
+    a.re = fma(-r.re, q.re, a.re);
+    a.re = fma(r.im, q.im, a.re);
+    a.im = fma(-r.re, q.im, a.im);
+    a.im = fma(-r.im, q.re, a.im);
+    return a;
+  } else {
+    return csub(a, cmul(r, q));
+  }
+}
+template <int L>
+__device__ __forceinline__ rl<L> acc_abs2(rl<L> s, const cx<L>& v) {
+  if constexpr (L == 1) {
+    return fma(v.im, v.im, fma(v.re, v.re, s));
+  } else {
+    return r_add(s, cabs2(v));
+  }
+}
+
 template <int L>
 __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
                          int warp, int T) {
@@ -223,7 +260,7 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
   rl<L> nrm_next = r_from<L>(0.0);
   if (warp == 0 && act) {
     rl<L> s = r_from<L>(0.0);
-    for (int i = 0; i < rows; ++i) s = r_add(s, cabs2(ld<L>(A, (int64_t)i * W, m, p)));
+    for (int i = 0; i < rows; ++i) s = acc_abs2<L>(s, ld<L>(A, (int64_t)i * W, m, p));
     nrm_next = s;
   }
   for (int q = 0; q < cols; ++q) {
@@ -244,14 +281,14 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
       if (!act) continue;
       cx<L> r = czero<L>();
       for (int i = 0; i < rows; ++i)
-        r = cadd(r, cconjmul(ld<L>(A, (int64_t)i * W + q, m, p), ld<L>(A, (int64_t)i * W + j, m, p)));
+        r = acc_conj_mul<L>(r, ld<L>(A, (int64_t)i * W + q, m, p), ld<L>(A, (int64_t)i * W + j, m, p));
       st<L>(R, (int64_t)q * W + j, m, p, r);
       rl<L> s = r_from<L>(0.0);
       for (int i = 0; i < rows; ++i) {
         int64_t e = (int64_t)i * W + j;
-        cx<L> v = csub(ld<L>(A, e, m, p), cmul(r, ld<L>(A, (int64_t)i * W + q, m, p)));
+        cx<L> v = sub_mul<L>(ld<L>(A, e, m, p), r, ld<L>(A, (int64_t)i * W + q, m, p));
         st<L>(A, e, m, p, v);
-        if (j == q + 1) s = r_add(s, cabs2(v));
+        if (j == q + 1) s = acc_abs2<L>(s, v);
       }
       if (j == q + 1) nrm_next = s;  // the owner of column q + 1 normalises it next
     }
@@ -260,7 +297,7 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
   if (warp == 0 && act) {
     for (int q = cols - 1; q >= 0; --q) {
       cx<L> acc = ld<L>(R, (int64_t)q * W + cols, m, p);
-      for (int j = q + 1; j < cols; ++j) acc = csub(acc, cmul(ld<L>(R, (int64_t)q * W + j, m, p), ld<L>(x, j, m, p)));
+      for (int j = q + 1; j < cols; ++j) acc = sub_mul<L>(acc, ld<L>(R, (int64_t)q * W + j, m, p), ld<L>(x, j, m, p));
       st<L>(x, q, m, p, cscale_r(acc, ld<L>(R, (int64_t)q * W + q, m, p).re));
     }
   }
