@@ -147,6 +147,18 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def max_over_ranks(x, world, dev):
+    """The largest of every rank's x (the job's time is its slowest rank's);
+    x itself on a single rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _traffic(L):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
     sources are unchanged since it was taken (else None)."""
@@ -439,10 +451,7 @@ def run_ours(a):
         dist.barrier()
     launch_ms = {L: [ev[s][L][0].elapsed_time(ev[s][L][1]) for s in range(a.steps)] for L in PRECISIONS}
     ms_step = sum(statistics.mean(launch_ms[L]) for L in PRECISIONS)
-    if world > 1:
-        t = torch.tensor([ms_step], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, world, dev)
     value = world * n / (ms_step * 1e-3)
 
     # end to end through the host-buffer entry point (pinned host memory)
@@ -460,11 +469,7 @@ def run_ours(a):
             for L in PRECISIONS:
                 ht.ht_eval_diff_host(sys_h[L], n, hx[L], hv[L], hj[L], stream)
             ts.append(time.perf_counter() - t0)
-        e2e_s = statistics.mean(ts)
-        if world > 1:
-            t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
+        e2e_s = max_over_ranks(statistics.mean(ts), world, dev)
         e2e = {"value": world * n / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(sum(hx[L].numel() * 8 for L in PRECISIONS)),
                "d2h_bytes_per_step": int(sum((hv[L].numel() + hj[L].numel()) * 8 for L in PRECISIONS))}
