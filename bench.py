@@ -34,7 +34,7 @@ import synth  # noqa: E402
 
 METRIC = "eval-diff pts/s (values + 32x32 Jacobian per point, complex D+DD+QD)"
 UNIT = "pts/s"
-WORKLOAD = "c1_evaldiff"
+WORKLOAD = "evaldiff_n32"
 PRECISIONS = (1, 2, 4)
 NAMES = {1: "D", 2: "DD", 4: "QD"}
 
@@ -93,7 +93,7 @@ def _args():
     p.add_argument("--n-pts", type=int, default=65536)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
-    p.add_argument("--track", default="c0_plain_d,c2_batched_dd",
+    p.add_argument("--track", default="plain_n6_d,batched_n12_dd",
                    help="tracking workloads to time as well (comma list, '' for none)")
     p.add_argument("--learned", type=int, default=65536,
                    help="paths of the held-out n = 16 double system for learned vs plain (0: skip)")
@@ -162,7 +162,7 @@ def max_over_ranks(x, world, dev):
 def _traffic(L):
     """DRAM bytes per launch from the committed ncu summary, if the kernel
     sources are unchanged since it was taken (else None)."""
-    path = os.path.join(ROOT, "profiles", "evaldiff_c1_65536pts.md")
+    path = os.path.join(ROOT, "profiles", "evaldiff_n32_65536pts.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
@@ -182,7 +182,7 @@ def _kernel_sha():
 
 # bounded oracle samples of the tracking workloads (first paths of the system
 # the GPU tracks; about 5-15 s each on the host cores)
-ORACLE_TRACK_SAMPLE = {"c0_plain_d": 64, "c2_batched_dd": 32, "c3_learned_d": 2048, "c4_stress_qd": 8}
+ORACLE_TRACK_SAMPLE = {"plain_n6_d": 64, "batched_n12_dd": 32, "learned_n16_d": 2048, "stress_n10_qd": 8}
 
 
 def oracle_track_rate(name, seed, limbs, h_min, sample):
@@ -215,7 +215,7 @@ def cpu_oracle_rate(system, budget_pts, threads=0, seed=77):
     return 1.0 / per_pt
 
 
-TRACK_LIMBS = {"c0_plain_d": 1, "c2_batched_dd": 2, "c3_learned_d": 1, "c4_stress_qd": 4}
+TRACK_LIMBS = {"plain_n6_d": 1, "batched_n12_dd": 2, "learned_n16_d": 1, "stress_n10_qd": 4}
 
 
 def track_workload(ht, torch, name, rank, world, reps=2):
@@ -227,7 +227,7 @@ def track_workload(ht, torch, name, rank, world, reps=2):
     deg = system.degrees()
     m = int(np.prod(deg.astype(np.int64)))
     gam = synth.random_gamma(cfg["seed"])
-    over = {"h_min": 0.01} if name == "c0_plain_d" else {"h_min": 1e-6}
+    over = {"h_min": 0.01} if name == "plain_n6_d" else {"h_min": 1e-6}
     prm = ht.ht_default_params(L, **over)
     hs = ht.system_from(system, L)
     n = system.n_vars
@@ -275,9 +275,9 @@ def _agreement(A, B, tol=1e-10):
 # rounds per path against 343 for 6 systems x 256 paths (same sample count
 # within 4x), for about 70 s of trace collection.
 LEARNED_CASES = {
-    "c3_learned_d": dict(limbs=1, check_limbs=2, eval_seed=3500, train_seeds=range(3000, 3200), train_paths=32,
+    "learned_n16_d": dict(limbs=1, check_limbs=2, eval_seed=3500, train_seeds=range(3000, 3200), train_paths=32,
                          epochs=20, warm_paths=None, tune_paths=4096),
-    "c4_stress_qd": dict(limbs=4, check_limbs=0, eval_seed=4000, train_seeds=range(4100, 4106), train_paths=256,
+    "stress_n10_qd": dict(limbs=4, check_limbs=0, eval_seed=4000, train_seeds=range(4100, 4106), train_paths=256,
                          epochs=30, warm_paths=1024, tune_paths=1024),
 }
 
@@ -519,10 +519,10 @@ def run_ours(a):
         if oracle_side:
             cfg = synth.CONFIGS[name]
             tracking[name]["cpu_baseline"] = oracle_track_rate(name, cfg["seed"], TRACK_LIMBS[name],
-                                                               0.01 if name == "c0_plain_d" else 1e-6,
+                                                               0.01 if name == "plain_n6_d" else 1e-6,
                                                                ORACLE_TRACK_SAMPLE[name])
-    for name, m, key in (("c3_learned_d", a.learned, "c3_learned_vs_plain"),
-                         ("c4_stress_qd", a.stress, "c4_learned_vs_plain")):
+    for name, m, key in (("learned_n16_d", a.learned, "learned_n16_d_vs_plain"),
+                         ("stress_n10_qd", a.stress, "stress_n10_qd_vs_plain")):
         if m > 0:
             tracking[key] = learned_vs_plain(ht, torch, world, name, m)
             if oracle_side:

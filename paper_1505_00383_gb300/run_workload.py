@@ -2,8 +2,8 @@
 
     python -m paper_1505_00383_gb300.run_workload WORKLOAD [--paths M] [--limbs L] [--h-min H]
 
-WORKLOAD is a tracking workload of synth.CONFIGS (c0_plain_d, c2_batched_dd,
-c3_learned_d, c4_stress_qd); the first M paths of its total-degree homotopy
+WORKLOAD is a tracking workload of synth.CONFIGS (plain_n6_d, batched_n12_dd,
+learned_n16_d, stress_n10_qd); the first M paths of its total-degree homotopy
 are tracked with the plain step rule through ht_track_paths_ex in L limbs
 (default: the workload's precision).  Used as the command of the tracker
 profiles; every step runs in libht.so.

@@ -240,13 +240,13 @@ def random_gamma(seed: int) -> tuple[float, float]:
 
 # The five workload families (seed = 1000 * family + instance).
 CONFIGS = {
-    "c0_plain_d": dict(kind="track", n=6, degree=2, n_monomials=8, limbs=1, seed=0),
-    "c1_evaldiff": dict(kind="evaldiff", n_vars=32, n_polys=32, n_monomials=64, k_min=2, k_max=8,
+    "plain_n6_d": dict(kind="track", n=6, degree=2, n_monomials=8, limbs=1, seed=0),
+    "evaldiff_n32": dict(kind="evaldiff", n_vars=32, n_polys=32, n_monomials=64, k_min=2, k_max=8,
                         e_min=1, e_max=3, n_pts=65536, seed=1000),
-    "c2_batched_dd": dict(kind="track", n=12, degree=2, n_monomials=16, limbs=2, seed=2000),
-    "c3_learned_d": dict(kind="track", n=16, degree=2, n_monomials=24, limbs=1, seed=3000,
+    "batched_n12_dd": dict(kind="track", n=12, degree=2, n_monomials=16, limbs=2, seed=2000),
+    "learned_n16_d": dict(kind="track", n=16, degree=2, n_monomials=24, limbs=1, seed=3000,
                          train_seeds=(3000, 3200), heldout_seeds=(3500, 3520)),
-    "c4_stress_qd": dict(kind="track", n=10, degree=3, n_monomials=32, limbs=4, seed=4000),
+    "stress_n10_qd": dict(kind="track", n=10, degree=3, n_monomials=32, limbs=4, seed=4000),
 }
 
 

@@ -50,11 +50,11 @@ def _check(system, x, L, val, jac, pts=None):
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
-@pytest.mark.parametrize("name", ["c0_plain_d", "c2_batched_dd", "c4_stress_qd", "c1_evaldiff"])
+@pytest.mark.parametrize("name", ["plain_n6_d", "batched_n12_dd", "stress_n10_qd", "evaldiff_n32"])
 def test_evaldiff_matches_oracle_several_tiles_and_ragged_tail(ht, name, L):
     s = synth.config_system(name)
     n = 32 * 3 + 5  # three full warps of points and a ragged tail of 5
-    if name == "c1_evaldiff" and L == 4:
+    if name == "evaldiff_n32" and L == 4:
         n = 32 + 3
     x = synth.unit_points(101 + L, s.n_vars, n, L)
     val, jac = _run(ht, s, x, L)
@@ -65,7 +65,7 @@ def test_evaldiff_matches_oracle_several_tiles_and_ragged_tail(ht, name, L):
 def test_evaldiff_full_size_sampled(ht, L):
     """The 65,536-point sweep in the launch configuration the benchmark times,
     checked on sampled points (first, last, and random ones)."""
-    s = synth.config_system("c1_evaldiff")
+    s = synth.config_system("evaldiff_n32")
     n = 65536
     x = synth.unit_points(1000 + L, s.n_vars, n, L)
     val, jac = _run(ht, s, x, L)
@@ -93,7 +93,7 @@ def test_edge_cases_wide_supports_constants_high_degree(ht, L):
 
 
 def test_zero_points_is_a_noop_and_bad_args_are_rejected(ht):
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     hs = ht.system_from(s, 1)
     x = torch.zeros((6, 2, 1, 4), dtype=torch.float64, device="cuda")
     val = torch.zeros((6, 2, 1, 4), dtype=torch.float64, device="cuda")
@@ -116,7 +116,7 @@ def test_zero_points_is_a_noop_and_bad_args_are_rejected(ht):
 def test_host_buffer_entry_point_matches(ht, L, n):
     """One block, two blocks and eight blocks with a ragged last block: the
     pipelined host entry gives the device entry's bits."""
-    s = synth.config_system("c2_batched_dd")
+    s = synth.config_system("batched_n12_dd")
     x = synth.unit_points(55, s.n_vars, n, L)
     v1, j1 = _run(ht, s, x, L)
     v2, j2 = _run(ht, s, x, L, host=True)
@@ -128,7 +128,7 @@ def test_every_kernel_configuration_gives_identical_results(ht, L):
     """Compact and unrolled monomial bodies, 64/128/256 threads: the same
     operations in the same order, so bitwise identical outputs; the autotuner
     then keeps one of them."""
-    s = synth.config_system("c1_evaldiff")
+    s = synth.config_system("evaldiff_n32")
     n = 32 * 5 + 7
     x = synth.unit_points(3 + L, s.n_vars, n, L)
     hs = ht.system_from(s, L)
@@ -168,13 +168,13 @@ def _run_variant(ht, system, x, L, variant):
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
-@pytest.mark.parametrize("name", ["c0_plain_d", "c2_batched_dd", "c4_stress_qd", "c1_evaldiff"])
+@pytest.mark.parametrize("name", ["plain_n6_d", "batched_n12_dd", "stress_n10_qd", "evaldiff_n32"])
 def test_integer_variant_matches_oracle(ht, name, L):
     """The integer-pipe evaluation (multi-limb integer complex arithmetic with
     fixed-point accumulation) meets the same tolerance against the oracle."""
     s = synth.config_system(name)
     n = 32 * 3 + 5
-    if name == "c1_evaldiff" and L == 4:
+    if name == "evaldiff_n32" and L == 4:
         n = 32 + 3
     x = synth.unit_points(201 + L, s.n_vars, n, L)
     val, jac = _run_variant(ht, s, x, L, 2)
@@ -183,7 +183,7 @@ def test_integer_variant_matches_oracle(ht, name, L):
 
 @pytest.mark.parametrize("L", [1, 2, 4])
 def test_integer_variant_full_size_sampled(ht, L):
-    s = synth.config_system("c1_evaldiff")
+    s = synth.config_system("evaldiff_n32")
     n = 65536
     x = synth.unit_points(3000 + L, s.n_vars, n, L)
     val, jac = _run_variant(ht, s, x, L, 2)

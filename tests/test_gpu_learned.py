@@ -100,7 +100,7 @@ def test_zero_network_tracks_exactly_like_the_plain_rule(ht):
     """rho = 0 proposes the plain rule's step, so the learned path machinery
     reproduces the plain tracker bitwise."""
     from paper_1505_00383_gb300 import learned
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     prm = ht.ht_default_params(1, h_min=1e-6)
     plain = learned.track(s, 1, gam, 64, prm)
@@ -114,7 +114,7 @@ def test_restart_from_recorded_states_reproduces_the_run(ht):
     """A path restarted from a recorded step start repeats the same arithmetic
     and ends where the uninterrupted run ended, bitwise."""
     from paper_1505_00383_gb300 import learned
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     prm = ht.ht_default_params(1, h_min=1e-6)
     full = learned.track(s, 1, gam, 64, prm)
@@ -137,7 +137,7 @@ def test_restart_from_recorded_states_reproduces_the_run(ht):
 
 def test_features_follow_their_definition(ht):
     from paper_1505_00383_gb300 import learned
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     prm = ht.ht_default_params(1, h_min=1e-6)
     rec = learned.collect_records(s, 1, gam, 16, prm, stride=3)
@@ -173,7 +173,7 @@ def test_labels_follow_their_definition(ht):
     point.  Probes re-run here one multiplier at a time; the predictor is
     re-derived from the record in numpy."""
     from paper_1505_00383_gb300 import learned
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     prm = ht.ht_default_params(1, h_min=1e-6)
     rec = learned.collect_records(s, 1, gam, 32, prm, stride=3)
@@ -241,11 +241,11 @@ def test_trained_network_gains_over_the_plain_rule(ht):
     and the same counts of converged, failed and diverged paths -- as the
     plain GPU tracker, and on a sample of paths as the oracle's tracker."""
     from paper_1505_00383_gb300 import learned
-    cfg = synth.CONFIGS["c3_learned_d"]
+    cfg = synth.CONFIGS["learned_n16_d"]
     prm = ht.ht_default_params(1, h_min=1e-9)
     feats, labs = [], []
     for seed in range(cfg["train_seeds"][0], cfg["train_seeds"][0] + 6):
-        s = synth.config_system("c3_learned_d", seed)
+        s = synth.config_system("learned_n16_d", seed)
         gam = synth.random_gamma(seed)
         rec = learned.collect_records(s, 1, gam, 256, prm, stride=2)
         labs.append(learned.step_labels(s, 1, gam, prm, rec))
@@ -254,7 +254,7 @@ def test_trained_network_gains_over_the_plain_rule(ht):
     assert losses[-1] < losses[0]
     tot_plain = tot_learn = 0
     for seed in range(cfg["heldout_seeds"][0], cfg["heldout_seeds"][0] + 2):
-        s = synth.config_system("c3_learned_d", seed)
+        s = synth.config_system("learned_n16_d", seed)
         gam = synth.random_gamma(seed)
         a = learned.track(s, 1, gam, 512, prm)
         b = learned.track(s, 1, gam, 512, prm, net=net)

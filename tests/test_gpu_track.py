@@ -163,10 +163,10 @@ def test_diagonal_system_closed_form(ht, L):
 
 
 @pytest.mark.parametrize("h_min", [0.01, 1e-6])
-def test_plain_tracker_c0_matches_oracle(ht, h_min):
+def test_plain_tracker_n6_matches_oracle(ht, h_min):
     """64 paths of the n = 6 total-degree homotopy in complex double, with the
     step range 0.01-0.1 of the workload and with a small step floor."""
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     g = track_gpu(ht, s, 1, 64, gamma=gam, h_min=h_min)
     o = track_oracle(s, 1, np.arange(64), gamma=gam, h_min=h_min)
@@ -181,7 +181,7 @@ def test_plain_tracker_c0_matches_oracle(ht, h_min):
 def test_team_size_and_launch_shape_do_not_change_results(ht):
     """Every team size splits the same arithmetic differently over warps but
     in the same order, so results are bitwise identical."""
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     base = track_gpu(ht, s, 1, 64, gamma=gam, team_warps=1, iters_per_launch=1, rounds_per_sync=2)
     for tw, it, rs in ((2, 4, 8), (4, 3, 4), (8, 7, 6), (0, 0, 0)):
@@ -194,7 +194,7 @@ def test_team_size_and_launch_shape_do_not_change_results(ht):
 def test_team_size_does_not_change_integer_evaluation_results(ht, L):
     """With f on the integer pipe each lane's arithmetic is the same for any
     split of polynomials and MGS columns over the team's warps."""
-    s = synth.config_system("c4_stress_qd" if L == 4 else "c2_batched_dd")
+    s = synth.config_system("stress_n10_qd" if L == 4 else "batched_n12_dd")
     gam = synth.random_gamma(1)
     base = track_gpu(ht, s, L, 96, gamma=gam, team_warps=1, iters_per_launch=2, rounds_per_sync=2)
     for tw in (2, 8):
@@ -206,7 +206,7 @@ def test_team_size_does_not_change_integer_evaluation_results(ht, L):
 def test_sharded_path_ranges_union_equals_full_run(ht):
     """Paths are independent (Section 1): tracking path ranges separately (as
     separate GPUs would) gives the full run's results."""
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     full = track_gpu(ht, s, 1, 64, gamma=gam, h_min=1e-6)
     parts = [track_gpu(ht, s, 1, 24, first=0, gamma=gam, h_min=1e-6),
@@ -216,8 +216,8 @@ def test_sharded_path_ranges_union_equals_full_run(ht):
     assert np.array_equal(x, full["x_end"]) and np.array_equal(st, full["status"])
 
 
-@pytest.mark.parametrize("name,L,m,sample,ev", [("c2_batched_dd", 2, 4096, 48, None), ("c2_batched_dd", 2, 4096, 24, 1),
-                                              ("c4_stress_qd", 4, 1024, 16, None), ("c4_stress_qd", 4, 512, 8, 1)])
+@pytest.mark.parametrize("name,L,m,sample,ev", [("batched_n12_dd", 2, 4096, 48, None), ("batched_n12_dd", 2, 4096, 24, 1),
+                                              ("stress_n10_qd", 4, 1024, 16, None), ("stress_n10_qd", 4, 512, 8, 1)])
 def test_batched_tracker_sampled_paths_match_oracle(ht, name, L, m, sample, ev):
     """The batched tracker on the workload shape (all 4,096 DD paths; 1,024 of
     the QD paths), with f evaluated on the integer pipe (the default for DD
@@ -241,7 +241,7 @@ def test_batched_tracker_sampled_paths_match_oracle(ht, name, L, m, sample, ev):
 
 
 def test_tracker_rejects_bad_arguments(ht):
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     hs = ht.system_from(s, 1)
     x = torch.zeros((6, 2, 1, 4), dtype=torch.float64, device="cuda")
     st = torch.zeros((4,), dtype=torch.int8, device="cuda")
@@ -264,7 +264,7 @@ def test_endpoint_check_in_higher_precision_matches_oracle(ht, L):
     double endpoints (polish_only, x0 with one limb): every path gives the
     oracle's own DD / QD endpoint of that path to working precision, and the
     last update is at the precision's level."""
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     m = 64
     g = track_gpu(ht, s, 1, m, gamma=gam, h_min=1e-9)
@@ -296,7 +296,7 @@ def test_narrow_start_points_are_widened(ht):
     """x0 given in one limb for a DD system: the missing limbs are zero, so
     the start solutions of x_i^2 - 1 (exactly +-1) give the same paths as the
     system's own start solutions."""
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     m = 64
     a = track_gpu(ht, s, 2, m, gamma=gam, h_min=1e-9)
@@ -314,7 +314,7 @@ def test_narrow_start_points_are_widened(ht):
 
 
 def test_endpoint_check_rejects_bad_arguments(ht):
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     hs = ht.system_from(s, 2)
     m = 4
     x = torch.zeros((6, 2, 2, m), dtype=torch.float64, device="cuda")
@@ -337,7 +337,7 @@ def test_track_autotuner_picks_a_valid_shape_and_keeps_results(ht):
     """ht_tune_track times every launch shape on a path sample and keeps the
     fastest in the system; tracking with the tuned defaults gives the same
     bits as any explicit shape."""
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     gam = synth.random_gamma(0)
     hs = ht.system_from(s, 1)
     p = ht.ht_default_params(1, h_min=1e-9)

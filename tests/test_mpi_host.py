@@ -129,7 +129,7 @@ def test_shift_accumulation_equals_generic(shim, L):
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
-@pytest.mark.parametrize("name", ["c0_plain_d", "c2_batched_dd", "c4_stress_qd", "c1_evaldiff", "edge", "spread"])
+@pytest.mark.parametrize("name", ["plain_n6_d", "batched_n12_dd", "stress_n10_qd", "evaldiff_n32", "edge", "spread"])
 def test_integer_evaluation_matches_oracle(oracle_lib, shim, L, name):
     """The integer evaluation path (bounds, fixed-point frame, reverse-mode
     sweep, conversion; the device kernel runs this code per lane) against the
@@ -151,13 +151,13 @@ def test_integer_evaluation_matches_oracle(oracle_lib, shim, L, name):
         x *= 2.0 ** rng.integers(-20, 20, nv * 6).reshape(nv, 1, 1, 6).astype(np.float64)
         x[2, :, :, 5] = 0.0
     elif name == "spread":  # points over 60 binades
-        s = synth.config_system("c4_stress_qd")
+        s = synth.config_system("stress_n10_qd")
         x = synth.unit_points(91 + L, s.n_vars, 8, L)
         rng = synth.SplitMix64(12)
         x *= 2.0 ** rng.integers(-30, 30, s.n_vars * 8).reshape(s.n_vars, 1, 1, 8).astype(np.float64)
     else:
         s = synth.config_system(name)
-        x = synth.unit_points(55 + L, s.n_vars, 2 if name == "c1_evaldiff" else 5, L)
+        x = synth.unit_points(55 + L, s.n_vars, 2 if name == "evaldiff_n32" else 5, L)
     n = x.shape[-1]
     nt = np.ascontiguousarray(s.n_terms, np.int32)
     ex = np.ascontiguousarray(s.exps, np.int8)

@@ -51,7 +51,7 @@ def test_naive_and_reverse_mode_agree(oracle_lib, L):
     """The product rule and the reverse mode are two different computations of
     the same derivatives; on both workload families they agree to rounding."""
     u = 2.0 ** (-53 * L)
-    for s, npts in ((synth.config_system("c0_plain_d"), 4), (synth.config_system("c1_evaldiff"), 1 if L == 4 else 2)):
+    for s, npts in ((synth.config_system("plain_n6_d"), 4), (synth.config_system("evaldiff_n32"), 1 if L == 4 else 2)):
         x = synth.unit_points(3, s.n_vars, npts, L)
         v1, j1 = oracle_lib.eval_(s, x, method="naive")
         v2, j2 = oracle_lib.eval_(s, x, method="speelpenning")

@@ -81,8 +81,8 @@ def test_dense_generic_system_reaches_bezout_and_precisions_agree(oracle_lib):
             assert r.absf() <= 1e-40
 
 
-def test_plain_c0_shape_runs_and_converged_endpoints_are_solutions(oracle_lib):
-    s = synth.config_system("c0_plain_d")
+def test_plain_n6_shape_runs_and_converged_endpoints_are_solutions(oracle_lib):
+    s = synth.config_system("plain_n6_d")
     out = oracle_lib.track(s, [2] * 6, synth.random_gamma(0), np.arange(64), 1,
                            oracle_lib.default_params(1, h_min=1e-6))
     assert np.all(out["status"] == 1)  # with a small step floor every path converges

@@ -15,7 +15,7 @@ def _params():
 
 def test_cache_tunes_once_per_key_and_reuses(tmp_path):
     path = str(tmp_path / "sub" / "tune.json")
-    s = synth.config_system("c0_plain_d")
+    s = synth.config_system("plain_n6_d")
     calls = []
 
     def fake(handle, deg, gamma, n, params):
@@ -38,9 +38,9 @@ def test_cache_tunes_once_per_key_and_reuses(tmp_path):
 
 
 def test_key_depends_on_shape_not_on_coefficients():
-    a = synth.config_system("c2_batched_dd")
-    b = synth.config_system("c2_batched_dd", 2001)
+    a = synth.config_system("batched_n12_dd")
+    b = synth.config_system("batched_n12_dd", 2001)
     assert tuning.cache_key(a, 2, "g") == tuning.cache_key(b, 2, "g")
-    c = synth.config_system("c0_plain_d")
+    c = synth.config_system("plain_n6_d")
     assert tuning.cache_key(a, 2, "g") != tuning.cache_key(c, 2, "g")
     assert tuning.cache_key(a, 2, "g").startswith("n=12;terms=%d;" % int(np.sum(a.n_terms)))
