@@ -483,7 +483,9 @@ def run_ours(a):
         achieved = work / (dom_ms * 1e-3)
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_peak / 1e12,
                     "unit": "T IMAD.WIDE/s", "frac": achieved / imad_peak, "traffic": tr,
-                    "kernel": "evaldiff_int_kernel<%d> (%s, integer limbs)" % (dom, NAMES[dom]),
+                    "kernel": "%s<%d> (%s, integer limbs)" % (
+                        "evaldiff_intblk_kernel" if tuned[NAMES[dom]]["threads"] == 256 else "evaldiff_int_kernel",
+                        dom, NAMES[dom]),
                     "work": "32x32->64-bit limb products of the complex multiplications",
                     "peak_source": "measured live: ht_bench_imad_rate (IMAD.WIDE chains on all SMs)"}
     else:

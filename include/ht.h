@@ -121,8 +121,12 @@ int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, doubl
  *              output (systems with at most 64 variables; HT_EUNSUPPORTED
  *              otherwise),
  *           -1 default (1)
- *   threads  CTA size 64, 128 or 256, or 0 for the default (128); variant 2
- *            always runs 128-thread CTAs
+ *   threads  CTA size 64, 128 or 256, or 0 for the default (128); for
+ *            variant 2, 128 (or 0, 64) runs one unit of 32 points and one
+ *            polynomial per warp with the lane's point in local memory, and
+ *            256 runs a block of 32 points per CTA with the block's points in
+ *            shared memory and the polynomials dealt to its 8 warps (the same
+ *            bits either way)
  * Variants 0 and 1 perform the same operations in the same order, so their
  * results are bitwise identical; variant 2 meets the same accuracy bound
  * (a small multiple of 2^(-53 L) times the sum of the moduli of the terms of

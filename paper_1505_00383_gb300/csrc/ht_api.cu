@@ -351,7 +351,7 @@ int ht_tune_eval(ht_system* s, int64_t n_pts, const double* x, double* val, doub
   int bv = 1, bt = 128;
   for (int vi = 0; vi < nvar && rc == HT_OK; ++vi)
     for (int ti = 0; ti < 3 && rc == HT_OK; ++ti) {
-      if (variants[vi] == 2 && ti > 0) continue;  // one CTA size for the integer variant
+      if (variants[vi] == 2 && ti == 1) continue;  // integer limbs: 128 (per unit) or 256 (per block)
       s->eval_variant = variants[vi];
       s->eval_threads = sizes[ti];
       rc = launch_evaldiff(s, n_pts, x, val, jac, st);  // warm-up

@@ -108,22 +108,79 @@ __global__ void __launch_bounds__(128, 4) evaldiff_int_kernel(EvalArgs a, const 
   }
 }
 
+// Block organisation of the same unit: a CTA takes a block of 32 points and
+// all polynomials, its warps dealing the polynomials round-robin.  The block's
+// converted points live once in shared memory (lane-interleaved, so every
+// access is a conflict-free 32-word row) instead of once per lane and unit
+// in local memory; the warp still walks one monomial with all lanes in step.
+// The sums are the same exact integers, so the results are those of the
+// per-unit kernel bit for bit.
+template <int L>
+__global__ void __launch_bounds__(256, 2) evaldiff_intblk_kernel(EvalArgs a, const mpi::fz<IntW<L>::W>* __restrict__ cfz,
+                                                              const float* __restrict__ clg) {
+  constexpr int W = IntW<L>::W;
+  using Z = mpi::fz<W>;
+  extern __shared__ __align__(16) int32_t xs[];  // [nv][2W+1][32] limb strings, then [nv][32] log2 moduli
+  float* lgs = reinterpret_cast<float*>(xs + (int64_t)a.nv * (2 * W + 1) * 32);
+  Z P[64];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, T = blockDim.x >> 5;
+  const int64_t n = a.v.npts, plane = (int64_t)a.nv * 2 * L * n, n_blocks = (n + 31) / 32;
+  const SmemPoints<L> X{xs, lane};
+  const SmemLog lg{lgs, lane};
+  for (int64_t b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+    const int64_t p = b * 32 + lane;
+    const bool live = p < n;
+    __syncthreads();  // the previous block's points are no longer read
+    for (int v = warp; v < a.nv; v += T) {
+      double re[L], im[L];
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        re[l] = live ? a.v.x[((int64_t)(v * 2) * L + l) * n + p] : 0.0;
+        im[l] = live ? a.v.x[((int64_t)(v * 2 + 1) * L + l) * n + p] : 0.0;
+      }
+      store_point<L>(xs, v, lane, mpi::from_doubles<W, L>(re, im));
+      lgs[v * 32 + lane] = mpi::log2_mod(re[0], im[0]);
+    }
+    __syncthreads();
+    if (!live) continue;  // lanes past the ragged tail sit the block out
+    for (int j = warp; j < a.np; j += T) {
+      double vre[L], vim[L];
+      int_row<L>(a.v.mon_off, a.v.pairs, cfz, clg, a.poly_off[j], a.poly_off[j + 1], X, lg, a.nv,
+                 a.jac + (int64_t)j * plane, n, p, vre, vim, P);
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        a.val[((int64_t)(j * 2) * L + l) * n + p] = vre[l];
+        a.val[((int64_t)(j * 2 + 1) * L + l) * n + p] = vim[l];
+      }
+    }
+  }
+}
+
 template <int L>
 static int launch_int(const EvalArgs& a, const ht_system* s, int threads, cudaStream_t st) {
-  {
+  const auto* cf = reinterpret_cast<const mpi::fz<IntW<L>::W>*>(s->d_coef_fz);
+  if (threads == 256) {  // block organisation (points in shared memory)
+    const size_t smem = (size_t)a.nv * 32 * ((2 * IntW<L>::W + 1) * sizeof(int32_t) + sizeof(float));
+    cudaFuncSetAttribute(evaldiff_intblk_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaldiff_intblk_kernel<L>, 256, smem);
+    if (per_sm < 1) per_sm = 1;
+    int64_t want = (a.v.npts + 31) / 32;
+    int64_t grid = (int64_t)sm_count() * per_sm;
+    if (grid > want) grid = want;
+    evaldiff_intblk_kernel<L><<<(unsigned)grid, 256, smem, st>>>(a, cf, s->d_coef_lg);
+  } else {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaldiff_int_kernel<L>, 128, 0);
     if (per_sm < 1) per_sm = 1;
     int64_t want = (a.n_units + 3) / 4;
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > want) grid = want;
-    (void)threads;
-    evaldiff_int_kernel<L><<<(unsigned)grid, 128, 0, st>>>(
-        a, reinterpret_cast<const mpi::fz<IntW<L>::W>*>(s->d_coef_fz), s->d_coef_lg);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff: launch");
-    return HT_OK;
+    evaldiff_int_kernel<L><<<(unsigned)grid, 128, 0, st>>>(a, cf, s->d_coef_lg);
   }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff: launch");
+  return HT_OK;
 }
 
 template <int L>

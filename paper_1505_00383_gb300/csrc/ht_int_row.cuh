@@ -69,13 +69,14 @@ __device__ __forceinline__ void int_point(const double* __restrict__ x, int nv, 
 
 // Monomials m0..m1 of one polynomial at the lane's point: the value as L
 // doubles per component (vre, vim) and the gradient written as doubles into
-// jrow ([nv][2][L][n], entry i at point p).  P is scratch for the forward
-// products (max monomial size entries).
-template <int L>
+// jrow ([nv][2][L][n], entry i at point p).  X and lg are indexable by
+// variable (local arrays or shared-memory views); P is scratch for the
+// forward products (max monomial size entries).
+template <int L, class XA, class LG>
 __device__ void int_row(const int32_t* __restrict__ mon_off, const uint16_t* __restrict__ pairs,
                         const mpi::fz<IntW<L>::W>* __restrict__ cfz, const float* __restrict__ clg, int m0, int m1,
-                        const mpi::fz<IntW<L>::W>* X, const float* lg, int nv, double* jrow, int64_t n, int64_t p,
-                        double* vre, double* vim, mpi::fz<IntW<L>::W>* P) {
+                        const XA& X, const LG& lg, int nv, double* jrow, int64_t n, int64_t p, double* vre,
+                        double* vim, mpi::fz<IntW<L>::W>* P) {
   constexpr int WA = IntW<L>::WA;
   int Fv[kIntMaxVars];
   const int F = mpi::frames_for_poly<WA>(mon_off, pairs, clg, m0, m1, lg, nv, Fv);
@@ -97,6 +98,44 @@ __device__ void int_row(const int32_t* __restrict__ mon_off, const uint16_t* __r
     mpi::fixed_to_doubles<WA, L>(ai, Fv[i], o);
 #pragma unroll
     for (int l = 0; l < L; ++l) jrow[((int64_t)(i * 2 + 1) * L + l) * n + p] = o[l];
+  }
+}
+
+// Views of a CTA's converted points in shared memory, lane-interleaved so a
+// warp's load of one word is 32 consecutive words: limb string words
+// [var][2W+1][32] (word 0 the exponent, then re limbs, then im limbs) and
+// log2 moduli [var][32].
+template <int L>
+struct SmemPoints {
+  static constexpr int W = IntW<L>::W, WORDS = 2 * W + 1;
+  const int32_t* x;
+  int lane;
+  __device__ __forceinline__ mpi::fz<W> operator[](int v) const {
+    const int32_t* q = x + (int64_t)v * WORDS * 32 + lane;
+    mpi::fz<W> z;
+    z.f = q[0];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      z.r[k] = q[(1 + k) * 32];
+      z.i[k] = q[(1 + W + k) * 32];
+    }
+    return z;
+  }
+};
+struct SmemLog {
+  const float* g;
+  int lane;
+  __device__ __forceinline__ float operator[](int v) const { return g[v * 32 + lane]; }
+};
+template <int L>
+__device__ __forceinline__ void store_point(int32_t* x, int v, int lane, const mpi::fz<IntW<L>::W>& z) {
+  constexpr int W = IntW<L>::W, WORDS = 2 * W + 1;
+  int32_t* q = x + (int64_t)v * WORDS * 32 + lane;
+  q[0] = z.f;
+#pragma unroll
+  for (int k = 0; k < W; ++k) {
+    q[(1 + k) * 32] = z.r[k];
+    q[(1 + W + k) * 32] = z.i[k];
   }
 }
 

@@ -47,9 +47,9 @@ HT_HD int frame_of(float E, int cnt) {
   const int Eint = (int)std::ceil((E > -3.0e4f ? E : -3.0e4f) + 1.0f) + head + 1;
   return Eint - (RB * (WA - 1) + 28);
 }
-template <int WA>
+template <int WA, class LG>
 HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const float* clg, int m0, int m1,
-                          const float* lg, int nv, int* Fv) {
+                          const LG& lg, int nv, int* Fv) {
   float Ev[64];
   for (int i = 0; i < nv; ++i) Ev[i] = -3.0e4f;
   float E = -3.0e4f;
@@ -89,9 +89,9 @@ HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const f
 // and a single accumulation site, so the multi-limb product is emitted once
 // (the 8-limb product is several hundred instructions) and its operands stay
 // in registers.
-template <int L, class Acc, class ValAdd>
+template <int L, class XA, class Acc, class ValAdd>
 HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m,
-                          const fz<IntW<L>::W>* X, const int* Fv, Acc& acc, ValAdd& val_add, fz<IntW<L>::W>* P) {
+                          const XA& X, const int* Fv, Acc& acc, ValAdd& val_add, fz<IntW<L>::W>* P) {
   constexpr int W = IntW<L>::W;
   using Z = fz<W>;
   enum : int { CHAIN, FWD, BWD0, BWD_D, BWD_S, LAST, DONE };
@@ -191,9 +191,11 @@ HT_HD int sweep_products(const uint16_t* pr, int k) {
 }
 
 // Value (fixed-point vr, vi in frame F) and gradient of the monomials m0..m1.
-template <int L, class Acc>
+// X is anything indexable by variable that yields the converted limb string
+// (a local array, or a view of shared memory).
+template <int L, class XA, class Acc>
 HT_HD void eval_poly_int(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m0, int m1,
-                         const fz<IntW<L>::W>* X, int F, const int* Fv, Acc& acc, int32_t* vr, int32_t* vi,
+                         const XA& X, int F, const int* Fv, Acc& acc, int32_t* vr, int32_t* vi,
                          fz<IntW<L>::W>* P) {
   constexpr int W = IntW<L>::W, WA = IntW<L>::WA;
   auto val_add = [&](const fz<W>& t) { acc_add_fast<W, WA>(vr, vi, t, 1, F); };

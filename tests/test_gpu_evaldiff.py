@@ -155,10 +155,10 @@ def test_every_kernel_configuration_gives_identical_results(ht, L):
         _check(s, x, L, val.cpu().numpy(), jac.cpu().numpy())
 
 
-def _run_variant(ht, system, x, L, variant):
+def _run_variant(ht, system, x, L, variant, threads=0):
     nv, _, _, n = x.shape
     hs = ht.system_from(system, L)
-    ht.ht_set_eval_config(hs, variant, 0)
+    ht.ht_set_eval_config(hs, variant, threads)
     xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     val = torch.full((system.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
     jac = torch.full((system.n_polys, nv, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
@@ -179,6 +179,22 @@ def test_integer_variant_matches_oracle(ht, name, L):
     x = synth.unit_points(201 + L, s.n_vars, n, L)
     val, jac = _run_variant(ht, s, x, L, 2)
     _check(s, x, L, val, jac)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("name", ["plain_n6_d", "stress_n10_qd", "evaldiff_n32"])
+def test_integer_block_organisation_is_bitwise_identical(ht, name, L):
+    """Integer limbs per unit (128-thread CTAs: lane = point, local copies of
+    the point) and per block of 32 points (256-thread CTAs: the block's points
+    in shared memory, polynomials dealt to warps) add the same exact terms:
+    the same bits, ragged last block included."""
+    s = synth.config_system(name)
+    n = 32 * 4 + 11 if L < 4 else 32 + 11
+    x = synth.unit_points(91 + L, s.n_vars, n, L)
+    a = _run_variant(ht, s, x, L, 2, 128)
+    b = _run_variant(ht, s, x, L, 2, 256)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    _check(s, x, L, b[0], b[1])
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
@@ -210,3 +226,5 @@ def test_integer_variant_edge_cases(ht, L):
     x[2, :, :, 5] = 0.0   # an exact zero variable at one point
     val, jac = _run_variant(ht, s, x, L, 2)
     _check(s, x, L, val, jac)
+    vb, jb = _run_variant(ht, s, x, L, 2, 256)
+    assert np.array_equal(val, vb) and np.array_equal(jac, jb)
