@@ -440,6 +440,10 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
   // L1 capacity from the Newton workspace.  Only warp 0's sample staging
   // lives in shared memory.
   __shared__ MlpWarpSmem mlp_stage;
+  // INT: the group's converted working points ([n][2W+1][32] words, then
+  // [n][32] log2 moduli), dynamic shared memory sized by the launcher
+  extern __shared__ __align__(16) int32_t xs_int[];
+  float* lgs_int = reinterpret_cast<float*>(xs_int + (int64_t)a.n * (2 * IntW<L>::W + 1) * 32);
   const int cap = a.prm.max_order + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, T = blockDim.x >> 5;
   const int n = a.n, W = n + 1;
@@ -552,12 +556,28 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
       __syncthreads();
       // ---- B: h(x, tt) = gamma (1 - tt) (x_j^d_j - 1) + tt f_j(x), Jacobian rows
       double pres = 0.0;
+      using Z = mpi::fz<IntW<L>::W>;
+      if constexpr (INT) {
+        // the group's working points, converted once into shared memory
+        // (warps take the coordinates round-robin; lanes without an active
+        // path store zeros), read by every warp's polynomials
+        for (int i = warp; i < n; i += T) {
+          double re[L], im[L];
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            re[l] = act ? a.xp[((int64_t)(i * 2) * L + l) * m + p] : 0.0;
+            im[l] = act ? a.xp[((int64_t)(i * 2 + 1) * L + l) * m + p] : 0.0;
+          }
+          store_point<L>(xs_int, i, lane, mpi::from_doubles<IntW<L>::W, L>(re, im));
+          lgs_int[i * 32 + lane] = mpi::log2_mod(re[0], im[0]);
+        }
+        __syncthreads();
+      }
       if (act) {
         cx<L> gs = cscale_r(gamma, r_diff<L>(1.0, tt));
-        using Z = mpi::fz<IntW<L>::W>;
-        Z X[INT ? kIntMaxTrack : 1], P[INT ? kIntMaxTrack : 1];
-        float lg[INT ? kIntMaxTrack : 1];
-        if constexpr (INT) int_point<L>(a.xp, n, m, p, X, lg);
+        Z P[INT ? kIntMaxTrack : 1];
+        const SmemPoints<L> X{xs_int, lane};
+        const SmemLog lg{lgs_int, lane};
         for (int j = warp; j < n; j += T) {
           double* Arow = a.A + (int64_t)j * rowA;
           cx<L> fj;
@@ -841,14 +861,17 @@ template <int L>
 int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_t st) {
   const bool learn = a.mlp_img != nullptr;
   const bool in = L > 1 && a.int_eval;  // the double tracker keeps FP64 evaluation
+  // dynamic shared memory of the integer instantiations: the converted points
+  const size_t dsm = in ? (size_t)a.n * 32 * ((2 * IntW<L>::W + 1) * sizeof(int32_t) + sizeof(float)) : 0;
   auto go = [&](auto kern) {
+    if (dsm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * team, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * team, dsm);
     if (per_sm < 1) per_sm = 1;
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > max_groups) grid = max_groups;
     if (grid < 1) grid = 1;
-    kern<<<(unsigned)grid, 32 * team, 0, st>>>(a);
+    kern<<<(unsigned)grid, 32 * team, dsm, st>>>(a);
   };
   if (learn)
     in ? go(track_kernel<L, true, L != 1>) : go(track_kernel<L, true, false>);
