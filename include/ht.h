@@ -296,6 +296,10 @@ int ht_compact(const int8_t* status, int64_t m, int32_t* path_idx, int32_t* coun
  *   t_end      device [n_paths]: t of the last accepted point
  *   steps      device [n_paths] (int32) steps per path, or NULL
  *   stats      host, or NULL
+ * Launch shape: p->team_warps warps per group of 32 paths and
+ * p->iters_per_launch Newton rounds per launch, or, where they are 0, the
+ * system's tuned shape (ht_tune_track) or the built-in one.  Results do not
+ * depend on the shape.
  * Blocks until every path has finished.  HT_ETIMEOUT if paths are still
  * active after the step limit allows (a bug guard).
  */
