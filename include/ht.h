@@ -415,10 +415,13 @@ int64_t ht_record_size(int n, int limbs, int max_order);
 /*
  * ht_step_features -- the 16 inputs of the learned step for each record
  * (device [n_rec][R] -> device [n_rec][16] floats), computed by the same device
- * code the tracker uses: t, log10 h, log10 |dx/dt|_inf / 4 (from the last two
- * accepted points), log10 of the last round's |dx|_inf and |h|_inf / 16, last
- * step's rounds / newton_max, last step rejected, nh / (max_order + 1),
- * log10(1 - t) / 16, each clamped to [-4, 4], then zeros.  Async.
+ * code the tracker uses, on the leading limbs: t, log10 h, log10 |dx/dt|_inf / 4
+ * (from the last two accepted points), log10 of the last round's |dx|_inf and
+ * |h|_inf / 16, last step's rounds / newton_max, last step rejected,
+ * nh / (max_order + 1), log10(1 - t) / 16, log10 of the curvature estimate
+ * 2 |second divided difference|_inf over the last three accepted points / 8
+ * (0 with fewer than three), log10(h / last accepted step) / 2 (0 with fewer
+ * than two), each clamped to [-4, 4], then zeros.  Async.
  */
 int ht_step_features(int n, int limbs, int max_order, int newton_max, int64_t n_rec, const double* records,
                      float* features, void* stream);
