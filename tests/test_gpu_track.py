@@ -7,6 +7,7 @@ import pytest
 
 import oracle
 import synth
+from certify import certify_roots
 from match import match_sets, to_complex
 from parity import TOL, cerr
 
@@ -238,6 +239,22 @@ def test_batched_tracker_sampled_paths_match_oracle(ht, name, L, m, sample, ev):
     e = cerr(sub["x_end"][..., conv], o["x_end"][..., conv])
     scale = np.maximum(1.0, np.max(np.abs(to_complex(o["x_end"][..., conv])), axis=1))
     assert np.all(np.max(e, axis=0) / scale <= 1e-10)
+
+
+@pytest.mark.parametrize("name,L", [("batched_n12_dd", 2), ("learned_n16_d", 1), ("stress_n10_qd", 4)])
+def test_full_workload_ends_at_all_roots(ht, name, L):
+    """Every path of the workload (4,096 DD, 65,536 D, 59,049 QD), in the
+    tracker's default launch shape at the step floor 1e-9: all converge, and
+    the GPU's endpoints carry a Kantorovich certificate of prod(d_i) distinct
+    isolated roots -- by Bezout all the roots, one per path."""
+    cfg = synth.CONFIGS[name]
+    s = synth.config_system(name)
+    m = cfg["degree"] ** cfg["n"]
+    g = track_gpu(ht, s, L, m, gamma=synth.random_gamma(cfg["seed"]), h_min=1e-9)
+    assert np.all(g["status"] == 1) and g["stats"]["converged"] == m
+    assert np.all(g["t_end"] == 1.0)
+    cert = certify_roots(s, to_complex(g["x_end"]))
+    assert cert["distinct_roots"] == m, cert
 
 
 def test_tracker_rejects_bad_arguments(ht):

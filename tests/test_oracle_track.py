@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 import synth
+from certify import certify_roots
 from exact import Cx, cx_from, poly_value
 from fractions import Fraction as Fr
 from match import match_sets, to_complex
@@ -93,3 +94,46 @@ def test_plain_n6_shape_runs_and_converged_endpoints_are_solutions(oracle_lib):
     assert D.min() > 1e-6
     val, _ = oracle_lib.eval_(s, out["x_end"])
     assert np.max(np.abs(val[:, 0, 0] + 1j * val[:, 1, 0])) < 1e-10
+    assert certify_roots(s, X)["distinct_roots"] == 64
+
+
+def test_certificate_catches_duplicates_and_non_roots(oracle_lib):
+    """The Kantorovich certificate accepts the closed-form roots of
+    x_i^2 = c_i, and refuses a list with a root twice (two paths on one root)
+    or with a point that is not near a root."""
+    c = np.array([0.3 + 0.8j, -1.1 + 0.2j, 0.5 - 0.9j])
+    s = _diag_system(c)
+    r = np.sqrt(c)
+    X = np.array([[r[0] * (1 - 2 * ((p >> 0) & 1)), r[1] * (1 - 2 * ((p >> 1) & 1)),
+                   r[2] * (1 - 2 * ((p >> 2) & 1))] for p in range(8)])
+    good = certify_roots(s, X)
+    assert good["distinct_roots"] == 8 and good["h"] < 1e-12
+    dup = X.copy()
+    dup[5] = dup[2]
+    assert certify_roots(s, dup)["distinct_roots"] == 0
+    off = X.copy()
+    off[3] = [0.1, 0.1j, 0.05]
+    bad = certify_roots(s, off)
+    assert bad["distinct_roots"] == 0 and bad["h"] > 0.5
+    near = X + 1e-7  # still certifies the same roots: each lies within 2 eta
+    assert certify_roots(s, near)["distinct_roots"] == 8
+
+
+@pytest.mark.parametrize("name", ["batched_n12_dd",
+                                  pytest.param("stress_n10_qd", marks=pytest.mark.slow),
+                                  pytest.param("learned_n16_d", marks=pytest.mark.slow)])
+def test_workload_systems_have_bezout_many_roots(oracle_lib, name):
+    """Pins the converged/failed/diverged split of the tracking workloads.
+    Tracked in double with the step floor 1e-9, every path converges, and the
+    endpoints carry a Kantorovich certificate of prod(d_i) distinct isolated
+    roots.  Bezout bounds the isolated roots by prod(d_i), so these are all of
+    them: every path of the total-degree homotopy ends at a finite regular
+    root, which is the split the tracker must report in every precision."""
+    cfg = synth.CONFIGS[name]
+    s = synth.config_system(name)
+    m = cfg["degree"] ** cfg["n"]
+    out = oracle_lib.track(s, [cfg["degree"]] * cfg["n"], synth.random_gamma(cfg["seed"]), np.arange(m), 1,
+                           oracle_lib.default_params(1, h_min=1e-9))
+    assert np.all(out["status"] == 1)
+    cert = certify_roots(s, to_complex(out["x_end"]))
+    assert cert["distinct_roots"] == m, cert
