@@ -221,6 +221,30 @@ def sparse_support_system(seed: int, n_vars: int, n_polys: int, n_monomials: int
     )
 
 
+def extreme_system(seed: int, n_vars: int, n_polys: int) -> System:
+    """A system at the limits of the format: random supports over n_vars
+    variables (6 monomials per polynomial, supports of 1..min(n_vars, 20)
+    variables, exponents 1..3), in which five monomials are replaced by a
+    support of the last 64 variables, x_{n/2}^127 (the largest exponent), a
+    constant, the first 64 variables squared, and the last variable alone.
+    Needs n_vars >= 64 and n_polys >= 3."""
+    if n_vars < 64 or n_polys < 3:
+        raise ValueError("extreme_system needs n_vars >= 64 and n_polys >= 3")
+    base = sparse_support_system(seed, n_vars, n_polys, 6, 1, min(n_vars, 20), 1, 3)
+    exps = base.exps.copy()
+    exps[0] = 0
+    exps[0, n_vars - 64:] = 1
+    exps[1] = 0
+    exps[1, n_vars // 2] = 127
+    exps[6] = 0
+    exps[7] = 0
+    exps[7, :64] = 2
+    exps[12] = 0
+    exps[12, n_vars - 1] = 1
+    return System(n_vars=n_vars, n_polys=n_polys, n_terms=base.n_terms, exps=exps, coef=base.coef,
+                  meta={"seed": seed, "family": "extreme"})
+
+
 def unit_points(seed: int, n_vars: int, n_pts: int, limbs: int) -> np.ndarray:
     """Points with |x_i| = 1 (to rounding in limb 0) and uniform phase; lower
     limbs are random non-overlapping tails.  Shape [n_vars][2][limbs][n_pts]."""

@@ -228,3 +228,43 @@ def test_integer_variant_edge_cases(ht, L):
     _check(s, x, L, val, jac)
     vb, jb = _run_variant(ht, s, x, L, 2, 256)
     assert np.array_equal(val, vb) and np.array_equal(jac, jb)
+
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_maximum_sizes_integer_variant_limit(ht, L):
+    """64 variables (the integer variant's largest system) with a 64-variable
+    monomial and exponent 127: the compact and unrolled FP64 bodies and both
+    integer organisations match the oracle, with one warp and a ragged tail
+    of points; FP64 bodies agree bitwise, and so do the integer ones."""
+    s = synth.extreme_system(77, 64, 3)
+    n = 32 + 5
+    x = synth.unit_points(17 + L, 64, n, L)
+    outs = {}
+    for variant, threads in ((1, 128), (0, 128), (2, 128), (2, 256)):
+        val, jac = _run_variant(ht, s, x, L, variant, threads)
+        _check(s, x, L, val, jac)
+        outs[(variant, threads)] = (val, jac)
+    for a, b in (((1, 128), (0, 128)), ((2, 128), (2, 256))):
+        assert np.array_equal(outs[a][0], outs[b][0]) and np.array_equal(outs[a][1], outs[b][1]), (a, b)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_maximum_sizes_255_variables(ht, L):
+    """255 variables, the largest system: the FP64 bodies match the oracle;
+    the integer variant (at most 64 variables) is refused with
+    HT_EUNSUPPORTED and the system keeps evaluating with its FP64 bodies."""
+    s = synth.extreme_system(78, 255, 4)
+    n = 32 + 3
+    x = synth.unit_points(27 + L, 255, n, L)
+    a = _run_variant(ht, s, x, L, 1, 128)
+    _check(s, x, L, *a)
+    hs = ht.system_from(s, L)
+    with pytest.raises(ht.HTError) as e:
+        ht.ht_set_eval_config(hs, 2, 0)
+    assert e.value.code == ht.HT_EUNSUPPORTED
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    val = torch.full((s.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    jac = torch.full((s.n_polys, 255, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    ht.ht_eval_diff(hs, n, xd, val, jac)
+    assert np.array_equal(val.cpu().numpy(), a[0]) and np.array_equal(jac.cpu().numpy(), a[1])

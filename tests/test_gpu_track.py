@@ -48,8 +48,23 @@ def test_mgs_solve_matches_oracle(ht, L, variant, rows, cols):
     """Both arithmetics against the oracle's MGS, within the conditioning
     bound at the variant's unit (2^-53L; for QD integer limbs the 204 bits a
     product keeps)."""
+    _mgs_case(ht, L, variant, rows, cols, 37)  # a full warp of systems and a ragged tail
+
+
+@pytest.mark.parametrize("L,variant", [(1, 0), (2, 2), (4, 2)])
+def test_mgs_solve_at_the_integer_row_limit(ht, L, variant):
+    """64 x 64, the largest system the integer variant takes (33 systems: a
+    warp and a ragged tail); 65 rows are refused with HT_EUNSUPPORTED."""
+    _mgs_case(ht, L, variant, 64, 64, 33)
+    if variant == 2:
+        buf = torch.zeros((65, 66, 2, L, 1), dtype=torch.float64, device="cuda")
+        with pytest.raises(ht.HTError) as e:
+            ht.ht_mgs_solve_ex(L, 2, 65, 65, 1, buf, buf, buf)
+        assert e.value.code == ht.HT_EUNSUPPORTED
+
+
+def _mgs_case(ht, L, variant, rows, cols, n_sys):
     rng = synth.SplitMix64(300 + rows * 7 + cols + L)
-    n_sys = 37  # a full warp of systems and a ragged tail
     re, im = synth.unit_circle(rng, n_sys * rows * (cols + 1))
     mag = rng.uniform(re.size) + 0.5
     Ab = np.zeros((rows, cols + 1, 2, L, n_sys))
@@ -255,6 +270,36 @@ def test_full_workload_ends_at_all_roots(ht, name, L):
     assert np.all(g["t_end"] == 1.0)
     cert = certify_roots(s, to_complex(g["x_end"]))
     assert cert["distinct_roots"] == m, cert
+
+
+@pytest.mark.parametrize("n", [32, 33])
+def test_tracker_at_the_integer_evaluation_limit(ht, n):
+    """n = 32 is the largest system whose DD and QD tracking evaluates on
+    integer limbs (QD also solves on them); n = 33 switches to the FP64 bodies
+    and FP64 least squares.  The last 8 of the 2^n paths (path indices past
+    2^32): DD against the oracle path by path; QD ends at the same roots, with
+    residuals at its own precision (the oracle's exact evaluation)."""
+    s = synth.total_degree_system(500 + n, n, 2, 4)
+    m = 8
+    first = 2 ** n - m
+    gam = synth.random_gamma(n)
+    g2 = track_gpu(ht, s, 2, m, first=first, gamma=gam, h_min=1e-6)
+    o2 = track_oracle(s, 2, np.arange(first, first + m), gamma=gam, h_min=1e-6)
+    assert np.array_equal(g2["status"], o2["status"]), (g2["status"], o2["status"])
+    conv = o2["status"] == 1
+    assert conv.sum() >= m // 2
+    scale = np.maximum(1.0, np.max(np.abs(to_complex(o2["x_end"][..., conv])), axis=1))
+    e = cerr(g2["x_end"][..., conv], o2["x_end"][..., conv])
+    assert np.all(np.max(e, axis=0) / scale <= 1e-10)
+    g4 = track_gpu(ht, s, 4, m, first=first, gamma=gam, h_min=1e-6)
+    assert np.array_equal(g4["status"], o2["status"])
+    d = np.abs(to_complex(g4["x_end"])[conv] - to_complex(g2["x_end"])[conv])
+    assert np.all(np.max(d, axis=1) / scale <= 1e-10)
+    pts = np.nonzero(conv)[0]
+    val, _ = oracle.eval_(s, g4["x_end"], pts=pts)
+    mag, _ = oracle.eval_magnitude(s, g4["x_end"], pts=pts)
+    res = np.hypot(val[:, 0, 0], val[:, 1, 0]) / mag
+    assert np.max(res) <= 1e-40, np.max(res)
 
 
 def test_tracker_rejects_bad_arguments(ht):

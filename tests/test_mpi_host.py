@@ -129,7 +129,8 @@ def test_shift_accumulation_equals_generic(shim, L):
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
-@pytest.mark.parametrize("name", ["plain_n6_d", "batched_n12_dd", "stress_n10_qd", "evaldiff_n32", "edge", "spread"])
+@pytest.mark.parametrize("name", ["plain_n6_d", "batched_n12_dd", "stress_n10_qd", "evaldiff_n32", "edge", "spread",
+                                  "extreme"])
 def test_integer_evaluation_matches_oracle(oracle_lib, shim, L, name):
     """The integer evaluation path (bounds, fixed-point frame, reverse-mode
     sweep, conversion; the device kernel runs this code per lane) against the
@@ -150,6 +151,9 @@ def test_integer_evaluation_matches_oracle(oracle_lib, shim, L, name):
         rng = synth.SplitMix64(4)
         x *= 2.0 ** rng.integers(-20, 20, nv * 6).reshape(nv, 1, 1, 6).astype(np.float64)
         x[2, :, :, 5] = 0.0
+    elif name == "extreme":  # 64 variables, a 64-variable support, exponent 127
+        s = synth.extreme_system(77, 64, 3)
+        x = synth.unit_points(17 + L, 64, 3, L)
     elif name == "spread":  # points over 60 binades
         s = synth.config_system("stress_n10_qd")
         x = synth.unit_points(91 + L, s.n_vars, 8, L)
@@ -219,14 +223,14 @@ def test_inverse_square_root_against_oracle(oracle_lib, shim, L):
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
-@pytest.mark.parametrize("rows,cols", [(6, 6), (12, 12), (9, 5), (1, 1)])
+@pytest.mark.parametrize("rows,cols", [(6, 6), (12, 12), (9, 5), (1, 1), (64, 64)])
 def test_least_squares_on_limb_strings_matches_oracle(oracle_lib, shim, L, rows, cols):
     """Modified Gram-Schmidt with every dot product and norm as one exact
     fixed-point sum, 1/sqrt by Newton: the solution of [A | b] against the
     oracle's MGS within the conditioning bound of the GPU test."""
     shim.mpi_mgs.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
     rng = synth.SplitMix64(300 + rows * 7 + cols + L)
-    n_sys = 12
+    n_sys = 12 if rows < 64 else 3  # 64 rows: the largest the integer variant takes
     re, im = synth.unit_circle(rng, n_sys * rows * (cols + 1))
     mag = rng.uniform(re.size) + 0.5
     Ab = np.zeros((n_sys, rows, cols + 1, 2, L))
