@@ -864,7 +864,9 @@ int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_
   // dynamic shared memory of the integer instantiations: the converted points
   const size_t dsm = in ? (size_t)a.n * 32 * ((2 * IntW<L>::W + 1) * sizeof(int32_t) + sizeof(float)) : 0;
   auto go = [&](auto kern) {
-    if (dsm > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
+    // the kernel's static shared memory counts against the same 48 KB default,
+    // so the limit is raised for any dynamic size (n = 32 DD asks for 48 KB)
+    if (dsm > 0) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dsm);
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * team, dsm);
     if (per_sm < 1) per_sm = 1;

@@ -440,10 +440,17 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
         crc = by_limbs(L, [&](auto c) { return launch_track_l<decltype(c)::value>(ar, team, groups, cs); });
         if (crc == HT_OK) crc = launch_compact(idx[r & 1], cnt[r & 1], status, idx[(r + 1) & 1], cnt[(r + 1) & 1], cs);
       }
+      graph = nullptr;
       cudaError_t ee = cudaStreamEndCapture(cs, &graph);
       cudaStreamDestroy(cs);
-      if (crc != HT_OK) return crc;
-      if (ee != cudaSuccess) return cuda_fail(ee, "ht_track_paths: end capture");
+      if (crc != HT_OK || ee != cudaSuccess) {
+        // a launch that failed inside the capture invalidates it; ending the
+        // capture then records that as the thread's last error, which would
+        // otherwise surface in the next call's launch checks
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        return crc != HT_OK ? crc : cuda_fail(ee, "ht_track_paths: end capture");
+      }
       ht_system::GraphEntry g;
       g.team = team;
       g.groups = groups;

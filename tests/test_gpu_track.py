@@ -275,10 +275,12 @@ def test_full_workload_ends_at_all_roots(ht, name, L):
 @pytest.mark.parametrize("n", [32, 33])
 def test_tracker_at_the_integer_evaluation_limit(ht, n):
     """n = 32 is the largest system whose DD and QD tracking evaluates on
-    integer limbs (QD also solves on them); n = 33 switches to the FP64 bodies
-    and FP64 least squares.  The last 8 of the 2^n paths (path indices past
-    2^32): DD against the oracle path by path; QD ends at the same roots, with
-    residuals at its own precision (the oracle's exact evaluation)."""
+    integer limbs (QD also solves on them, and DD asks for exactly 48 KB of
+    dynamic shared memory); n = 33 switches to the FP64 bodies.  The last 8
+    of the 2^n paths (path indices past 2^32): DD against the oracle path by
+    path; at n = 32, QD ends at the same roots with residuals at its own
+    precision (the oracle's exact evaluation).  QD on FP64 bodies is covered
+    at n = 10 (ev = 1 above); eight paths of it at n = 33 take minutes."""
     s = synth.total_degree_system(500 + n, n, 2, 4)
     m = 8
     first = 2 ** n - m
@@ -291,6 +293,8 @@ def test_tracker_at_the_integer_evaluation_limit(ht, n):
     scale = np.maximum(1.0, np.max(np.abs(to_complex(o2["x_end"][..., conv])), axis=1))
     e = cerr(g2["x_end"][..., conv], o2["x_end"][..., conv])
     assert np.all(np.max(e, axis=0) / scale <= 1e-10)
+    if n > 32:
+        return
     g4 = track_gpu(ht, s, 4, m, first=first, gamma=gam, h_min=1e-6)
     assert np.array_equal(g4["status"], o2["status"])
     d = np.abs(to_complex(g4["x_end"])[conv] - to_complex(g2["x_end"])[conv])
