@@ -272,11 +272,13 @@ def test_full_workload_ends_at_all_roots(ht, name, L):
     assert cert["distinct_roots"] == m, cert
 
 
-@pytest.mark.parametrize("n", [32, 33])
+@pytest.mark.parametrize("n", [20, 32, 33])
 def test_tracker_at_the_integer_evaluation_limit(ht, n):
     """n = 32 is the largest system whose DD and QD tracking evaluates on
     integer limbs (QD also solves on them, and DD asks for exactly 48 KB of
-    dynamic shared memory); n = 33 switches to the FP64 bodies.  The last 8
+    dynamic shared memory); n = 33 switches to the FP64 bodies; at n = 20 the
+    QD kernel's dynamic shared memory is under 48 KB but, with its static
+    shared memory, over the default limit.  The last 8
     of the 2^n paths (path indices past 2^32): DD against the oracle path by
     path; at n = 32, QD ends at the same roots with residuals at its own
     precision (the oracle's exact evaluation).  QD on FP64 bodies is covered
