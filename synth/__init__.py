@@ -221,6 +221,18 @@ def sparse_support_system(seed: int, n_vars: int, n_polys: int, n_monomials: int
     )
 
 
+def deficient_system() -> System:
+    """f = (xy - 1, xy + x - 2): total degrees (2, 2), Bezout number 4, but the
+    only finite root is (1, 1) (subtracting gives x = 1), where
+    det J = det [[1, 1], [2, 1]] = -1: regular.  The leading forms xy, xy
+    vanish at [1:0:0] and [0:1:0], so three paths of the total-degree
+    homotopy must leave every bounded set."""
+    exps = np.array([[1, 1], [0, 0], [1, 1], [1, 0], [0, 0]], np.int8)
+    coef = np.array([[1, 0], [-1, 0], [1, 0], [1, 0], [-2, 0]], float)
+    return System(n_vars=2, n_polys=2, n_terms=np.array([2, 3], np.int32), exps=exps, coef=coef,
+                  meta={"family": "deficient"})
+
+
 def extreme_system(seed: int, n_vars: int, n_polys: int) -> System:
     """A system at the limits of the format: random supports over n_vars
     variables (6 monomials per polynomial, supports of 1..min(n_vars, 20)

@@ -308,6 +308,25 @@ def test_tracker_at_the_integer_evaluation_limit(ht, n):
     assert np.max(res) <= 1e-40, np.max(res)
 
 
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("h_max", [0.1, 0.005])
+def test_deficient_system_matches_oracle_path_by_path(ht, L, h_max):
+    """Bezout number 4, one finite root: paths that diverge past r_div, fail,
+    or (with the default step cap) jump onto the root's path -- the same
+    outcome as the oracle for every path, including where it ended."""
+    s = synth.deficient_system()
+    gam = synth.random_gamma(5)
+    over = dict(r_div=1e4, h_min=1e-8, h_max=h_max)
+    g = track_gpu(ht, s, L, 4, gamma=gam, **over)
+    o = track_oracle(s, L, np.arange(4), gamma=gam, **over)
+    assert np.array_equal(g["status"], o["status"]), (g["status"], o["status"])
+    assert np.sum(g["status"] == 1) == (1 if h_max < 0.01 else 3)
+    conv = o["status"] == 1
+    e = cerr(g["x_end"][..., conv], o["x_end"][..., conv])
+    assert np.max(e) <= 1e-10
+    assert np.all(g["t_end"][~conv] > 0.999)  # the others leave near t = 1
+
+
 def test_tracker_rejects_bad_arguments(ht):
     s = synth.config_system("plain_n6_d")
     hs = ht.system_from(s, 1)

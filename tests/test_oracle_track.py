@@ -137,3 +137,26 @@ def test_workload_systems_have_bezout_many_roots(oracle_lib, name):
     assert np.all(out["status"] == 1)
     cert = certify_roots(s, to_complex(out["x_end"]))
     assert cert["distinct_roots"] == m, cert
+
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_deficient_system_one_root_and_paths_to_infinity(oracle_lib, L):
+    """With the step cap 0.005 exactly one path converges, to (1, 1), and the
+    other three do not (diverged past r_div or failed), as the root count
+    demands.  With the default cap 0.1 two more paths jump onto the root's
+    path and report it as their endpoint; the certificate refuses those
+    endpoints as distinct roots."""
+    s = synth.deficient_system()
+    gam = synth.random_gamma(5)
+    tight = oracle_lib.track(s, [2, 2], gam, np.arange(4), L,
+                             oracle_lib.default_params(L, r_div=1e4, h_min=1e-8, h_max=0.005))
+    st = tight["status"]
+    assert np.sum(st == 1) == 1 and np.all(np.isin(st, (1, -1, -2))) and np.sum(st == -2) >= 1
+    X = to_complex(tight["x_end"])[st == 1]
+    assert np.max(np.abs(X - 1.0)) <= {1: 1e-12, 2: 1e-28, 4: 1e-55}[L]
+    loose = oracle_lib.track(s, [2, 2], gam, np.arange(4), L, oracle_lib.default_params(L, r_div=1e4, h_min=1e-8))
+    conv = to_complex(loose["x_end"])[loose["status"] == 1]
+    assert conv.shape[0] == 3 and np.max(np.abs(conv - 1.0)) < 1e-10
+    assert certify_roots(s, conv)["distinct_roots"] == 0
+    assert certify_roots(s, conv[:1])["distinct_roots"] == 1
