@@ -13,10 +13,13 @@ Every function follows a passage of Verschelde & Yu (2015):
   * ``compact``          Table tabjobidx scan and path_idx;
   * ``start_solutions``  roots of x_i^d_i - 1 for the homotopy of Eq. eqlinhom;
   * ``track``            the predictor-corrector loop of Section 2;
-  * ``real_op``          L-limb arithmetic (double, double double, quad double).
+  * ``real_op``          L-limb arithmetic (double, double double, quad double);
+  * ``predict``, ``homotopy``  the tracker's extrapolation predictor and the
+                         homotopy of Eq. eqlinhom with its Jacobian, alone.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 import os
 import subprocess
@@ -51,33 +54,72 @@ def lib():
     with _lock:
         if _lib is None:
             build()
-            L = ctypes.CDLL(_LIB)
-            P = ctypes.c_void_p
-            i32, i64 = ctypes.c_int, ctypes.c_int64
-            sig = {
-                "hto_version": ([], i32),
-                "hto_param_count": ([], i32),
-                "hto_real_op": ([i32, i32, i64, P, P, P], i32),
-                "hto_value_diff": ([i32, i64, P, P, P], i32),
-                "hto_eval": ([i32, i32, i32, i32, P, P, P, i64, P, i64, P, P, P, i32], i32),
-                "hto_eval_magnitude": ([i32, i32, i32, P, P, P, i64, P, i64, P, P, P], i32),
-                "hto_speelpenning_slots": ([i32, i32, P, P], i32),
-                "hto_mgs_solve": ([i32, i32, i32, i64, P, P, P], i32),
-                "hto_start_solutions": ([i32, i32, P, i64, i64, P], i32),
-                "hto_compact": ([P, i64, P, P], i64),
-                "hto_track": ([i32, i32, P, P, P, P, P, i64, P, P, i32, P, P, P, P, P, P], i32),
-                "hto_mlp_nparam": ([], i32),
-                "hto_mlp_forward": ([i64, P, P, P], i32),
-                "hto_mlp_loss_grad": ([i64, P, P, P, P], ctypes.c_double),
-                "hto_adam_step": ([i64, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                   ctypes.c_double, i32], i32),
-            }
-            for name, (args, res) in sig.items():
-                f = getattr(L, name)
-                f.argtypes = args
-                f.restype = res
-            _lib = L
+            _lib = _open(_LIB)
     return _lib
+
+
+@contextlib.contextmanager
+def loaded_from(path: str):
+    """Run the wrappers against another build of the oracle source for the
+    duration of the block: the planted-mistake copies that check the pins
+    catch mistakes."""
+    global _lib
+    other = _open(path)
+    with _lock:
+        saved, _lib = _lib, other
+    try:
+        yield
+    finally:
+        with _lock:
+            _lib = saved
+
+
+def compile_variant(source: str, out: str) -> str:
+    """Compile C++ source text with the oracle's own flags into the shared
+    library `out` (used for the planted-mistake copies)."""
+    src = out + ".cpp"
+    with open(src, "w") as f:
+        f.write(source)
+    subprocess.check_call(["g++", "-std=c++17", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared",
+                           "-pthread", "-o", out, src])
+    return out
+
+
+def source() -> str:
+    with open(_SRC) as f:
+        return f.read()
+
+
+def _open(path: str):
+    """Load a build of the oracle and declare its entry points."""
+    L = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    i32, i64 = ctypes.c_int, ctypes.c_int64
+    sig = {
+        "hto_version": ([], i32),
+        "hto_param_count": ([], i32),
+        "hto_real_op": ([i32, i32, i64, P, P, P], i32),
+        "hto_value_diff": ([i32, i64, P, P, P], i32),
+        "hto_eval": ([i32, i32, i32, i32, P, P, P, i64, P, i64, P, P, P, i32], i32),
+        "hto_eval_magnitude": ([i32, i32, i32, P, P, P, i64, P, i64, P, P, P], i32),
+        "hto_speelpenning_slots": ([i32, i32, P, P], i32),
+        "hto_mgs_solve": ([i32, i32, i32, i64, P, P, P], i32),
+        "hto_start_solutions": ([i32, i32, P, i64, i64, P], i32),
+        "hto_compact": ([P, i64, P, P], i64),
+        "hto_track": ([i32, i32, P, P, P, P, P, i64, P, P, i32, P, P, P, P, P, P], i32),
+        "hto_predict": ([i32, i32, i32, P, P, ctypes.c_double, P], i32),
+        "hto_homotopy": ([i32, i32, P, P, P, P, P, ctypes.c_double, i64, P, P, P], i32),
+        "hto_mlp_nparam": ([], i32),
+        "hto_mlp_forward": ([i64, P, P, P], i32),
+        "hto_mlp_loss_grad": ([i64, P, P, P, P], ctypes.c_double),
+        "hto_adam_step": ([i64, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                           ctypes.c_double, i32], i32),
+    }
+    for name, (args, res) in sig.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    return L
 
 
 def _p(a):
@@ -215,6 +257,31 @@ def track(system, start_degrees, gamma, path_ids, limbs: int, params: dict | Non
                          _p(out["rejects"]), _p(out["newton"]))
     assert rc == 0
     return out
+
+
+def predict(ts: np.ndarray, xs: np.ndarray, t1: float) -> np.ndarray:
+    """The tracker's extrapolation predictor (Section 2): through the points
+    (ts[j], xs[j]), xs [m][n][2][L], to t1; returns [n][2][L]."""
+    ts = _c(ts, np.float64)
+    xs = _c(xs, np.float64)
+    m, n, _, L = xs.shape
+    out = np.empty((n, 2, L))
+    assert lib().hto_predict(L, n, m, _p(ts), _p(xs), float(t1), _p(out)) == 0
+    return out
+
+
+def homotopy(system, start_degrees, gamma, t: float, x: np.ndarray):
+    """gamma (1 - t) g(x) + t f(x) (Eq. eqlinhom, g_i = x_i^d_i - 1) and its
+    Jacobian in x at x [n][2][L][n_pts]: h [n][2][L][n_pts], J [n][n][2][L][n_pts]."""
+    x = _c(x, np.float64)
+    n, _, L, n_pts = x.shape
+    nt, ex, cf = _sys_args(system, L)
+    d = _c(start_degrees, np.int32)
+    g = _c(np.array(gamma, dtype=np.float64), np.float64)
+    h = np.empty((n, 2, L, n_pts))
+    J = np.empty((n, n, 2, L, n_pts))
+    assert lib().hto_homotopy(L, n, _p(nt), _p(ex), _p(cf), _p(d), _p(g), float(t), n_pts, _p(x), _p(h), _p(J)) == 0
+    return h, J
 
 
 # ------------------------------------------------------------------ learned step

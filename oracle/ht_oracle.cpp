@@ -38,13 +38,6 @@
 namespace {
 
 // ---------------------------------------------------------------- exact sums
-// Knuth's two-sum: s + e == a + b exactly.
-inline void two_sum(double a, double b, double& s, double& e) {
-  s = a + b;
-  double bv = s - a;
-  e = (a - (s - bv)) + (b - bv);
-}
-
 // Veltkamp's split of a double into two 26-bit halves.
 inline void split(double a, double& hi, double& lo) {
   double c = 134217729.0 * a;  // 2^27 + 1
@@ -878,6 +871,48 @@ int track_batch(int n, const int32_t* n_terms, const int8_t* exps, const double*
   return 0;
 }
 
+// The predictor alone: m points (ts [m], xs [m][n][2][L]) extrapolated to t1
+// (out [n][2][L]).
+template <int L>
+int predict_one(int n, int m, const double* ts, const double* xs, double t1, double* out) {
+  std::vector<double> ht(ts, ts + m);
+  std::vector<std::vector<C<L>>> hx(m, std::vector<C<L>>(n));
+  for (int j = 0; j < m; ++j)
+    for (int i = 0; i < n; ++i)
+      for (int l = 0; l < L; ++l) {
+        hx[j][i].re.v[l] = xs[(((size_t)j * n + i) * 2 + 0) * L + l];
+        hx[j][i].im.v[l] = xs[(((size_t)j * n + i) * 2 + 1) * L + l];
+      }
+  std::vector<C<L>> o(n);
+  predict<L>(ht, hx, m, t1, o);
+  for (int i = 0; i < n; ++i)
+    for (int l = 0; l < L; ++l) {
+      out[(i * 2 + 0) * L + l] = o[i].re.v[l];
+      out[(i * 2 + 1) * L + l] = o[i].im.v[l];
+    }
+  return 0;
+}
+
+// The homotopy alone: h(x, t) [n][2][L][n_pts] and its Jacobian in x
+// [n][n][2][L][n_pts] at the points x [n][2][L][n_pts].
+template <int L>
+int homotopy_points(int n, const int32_t* n_terms, const int8_t* exps, const double* coef, const int32_t* start_deg,
+                    const double* gamma, double t, int64_t n_pts, const double* x, double* h, double* J) {
+  Homotopy<L> H;
+  H.f = make_sys<L>(n, n, n_terms, exps, coef);
+  H.d.assign(start_deg, start_deg + n);
+  H.gamma = C<L>{rfrom<L>(gamma[0]), rfrom<L>(gamma[1])};
+  H.deg_max = H.f.max_deg;
+  std::vector<C<L>> xv(n), hv(n), Jv((size_t)n * n);
+  for (int64_t p = 0; p < n_pts; ++p) {
+    for (int i = 0; i < n; ++i) xv[i] = load_soa<L>(x, i, p, n_pts);
+    eval_homotopy<L>(H, xv.data(), t, hv.data(), Jv.data());
+    for (int i = 0; i < n; ++i) store_soa<L>(h, i, p, n_pts, hv[i]);
+    for (size_t e = 0; e < Jv.size(); ++e) store_soa<L>(J, (int64_t)e, p, n_pts, Jv[e]);
+  }
+  return 0;
+}
+
 }  // namespace
 
 template <template <int> class F, typename... A>
@@ -894,6 +929,8 @@ template <int L> struct MagF { template <typename... A> static int run(A... a) {
 template <int L> struct MgsF { template <typename... A> static int run(A... a) { return mgs_batch<L>(a...); } };
 template <int L> struct StartF { template <typename... A> static int run(A... a) { return start_batch<L>(a...); } };
 template <int L> struct TrackF { template <typename... A> static int run(A... a) { return track_batch<L>(a...); } };
+template <int L> struct PredF { template <typename... A> static int run(A... a) { return predict_one<L>(a...); } };
+template <int L> struct HomF { template <typename... A> static int run(A... a) { return homotopy_points<L>(a...); } };
 template <int L>
 struct SlotsF {
   static int run(int k, const double* x, double* slots) {
@@ -993,6 +1030,22 @@ int hto_speelpenning_slots(int L, int k, const double* x, double* slots) {
 // A: [n_sys][rows][cols][2][L], b: [n_sys][rows][2][L], x: [n_sys][cols][2][L].
 int hto_mgs_solve(int L, int rows, int cols, int64_t n_sys, const double* A, const double* b, double* x) {
   return dispatch_l<MgsF>(L, rows, cols, n_sys, A, b, x);
+}
+
+// The tracker's extrapolation predictor (Section 2) through m points:
+// ts [m], xs [m][n][2][L] -> out [n][2][L], the extrapolated point at t1.
+int hto_predict(int L, int n, int m, const double* ts, const double* xs, double t1, double* out) {
+  if (n < 1 || m < 1) return -1;
+  return dispatch_l<PredF>(L, n, m, ts, xs, t1, out);
+}
+
+// The homotopy gamma (1 - t) g(x) + t f(x) of Eq. eqlinhom, g_i = x_i^d_i - 1,
+// and its Jacobian in x at the points x [n][2][L][n_pts]:
+// h [n][2][L][n_pts], J [n][n][2][L][n_pts].
+int hto_homotopy(int L, int n, const int32_t* n_terms, const int8_t* exps, const double* coef,
+                 const int32_t* start_deg, const double* gamma, double t, int64_t n_pts, const double* x, double* h,
+                 double* J) {
+  return dispatch_l<HomF>(L, n, n_terms, exps, coef, start_deg, gamma, t, n_pts, x, h, J);
 }
 
 // Start solutions of x_i^d_i - 1 = 0 for paths first..first+count-1:

@@ -1,0 +1,114 @@
+"""Planted mistakes in the oracle, on the CPU.
+
+Each entry copies the oracle's source with one plausible mistake (a dropped
+term, a wrong sign, a wrong index or constant), compiles the copy with the
+oracle's own flags, and runs one pin against it: the pin must fail.  This
+checks that the pins would catch such mistakes in the oracle, not only that
+the oracle passes them.  The mistakes are planted in the oracle only; the
+CUDA library is not involved.
+"""
+import os
+import re
+from concurrent.futures import ThreadPoolExecutor
+
+import pytest
+
+import oracle
+import test_oracle_arith as A
+import test_oracle_eval as E
+import test_oracle_mgs_start_compact as M
+import test_oracle_mlp as N
+import test_oracle_track as T
+
+# name: (original line, planted mistake, the pin that must fail)
+MUTANTS = {
+    "accumulator drops the rounding error of a sum": (
+        "double lo = y - (hi - x);", "double lo = 0.0 * (y - (hi - x));",
+        lambda o: A.test_real_op_against_exact_rationals(o, 2, "add")),
+    "Dekker product drops the low-by-low term": (
+        "e = ((ah * bh - p) + ah * bl + al * bh) + al * bl;", "e = ((ah * bh - p) + ah * bl + al * bh);",
+        lambda o: A.test_real_op_against_exact_rationals(o, 2, "mul")),
+    "division stops after one quotient digit": (
+        "for (int it = 0; it < L + 2; ++it) {", "for (int it = 0; it < 1; ++it) {",
+        lambda o: A.test_real_op_against_exact_rationals(o, 2, "div")),
+    "square root takes one Newton step": (
+        "for (int it = 0; it < L; ++it) y = rmul<L>", "for (int it = 0; it < 1; ++it) y = rmul<L>",
+        lambda o: A.test_sqrt_against_exact(o, 4)),
+    "product rule keeps the differentiated exponent": (
+        "int e = a[l] - (l == i ? 1 : 0);", "int e = a[l] - (l == i ? 0 : 0);",
+        lambda o: E.test_eval_against_exact_brute_force(o, 1, "naive")),
+    "reverse mode takes the wrong forward product": (
+        "slots[out] = cmul<L>(slots[j - 2], slots[k - 1]);", "slots[out] = cmul<L>(slots[j - 1], slots[k - 1]);",
+        lambda o: E.test_tabmoneval_slots(o)),
+    "common factor misses one power": (
+        "for (int e = 1; e < a[i]; ++e) cf = cmul<L>(cf, x[i]);", "for (int e = 2; e < a[i]; ++e) cf = cmul<L>(cf, x[i]);",
+        lambda o: E.test_eval_against_exact_brute_force(o, 1, "speelpenning")),
+    "derivative not scaled by the exponent": (
+        "C<L> scaled = cscale<L>(cf, rfrom<L>((double)ex[r]));", "C<L> scaled = cf;",
+        lambda o: E.test_eval_against_exact_brute_force(o, 1, "speelpenning")),
+    "Gram-Schmidt projection without the conjugate": (
+        "r = cadd<L>(r, cconjmul<L>(M[(size_t)i * W + q], M[(size_t)i * W + j]));",
+        "r = cadd<L>(r, cmul<L>(M[(size_t)i * W + q], M[(size_t)i * W + j]));",
+        lambda o: M.test_mgs_matches_lstsq_in_double(o, 6, 6)),
+    "back substitution adds instead of subtracting": (
+        "acc = csub<L>(acc, cmul<L>(Rm[(size_t)q * W + j], x[j]));",
+        "acc = cadd<L>(acc, cmul<L>(Rm[(size_t)q * W + j], x[j]));",
+        lambda o: M.test_mgs_matches_lstsq_in_double(o, 6, 6)),
+    "roots of unity at half the angle": (
+        "double th = 2.0 * pi * (double)k / (double)d;", "double th = pi * (double)k / (double)d;",
+        lambda o: M.test_start_solutions_are_the_roots_of_unity(o, 1, [5, 3])),
+    "path digits in the wrong radix": (
+        "    r /= deg[i];\n", "    r /= 2;\n",
+        lambda o: M.test_start_solutions_are_the_roots_of_unity(o, 1, [3, 2])),
+    "compaction keeps finished paths": (
+        "if (status[i] == 0) path_idx[c++] = (int32_t)i;", "if (status[i] >= 0) path_idx[c++] = (int32_t)i;",
+        lambda o: M.test_compaction_table_tabjobidx(o)),
+    "homotopy weights g by t instead of 1 - t": (
+        "C<L> gs = cscale<L>(H.gamma, omt);", "C<L> gs = cscale<L>(H.gamma, tt);",
+        lambda o: T.test_homotopy_special_cases_and_affinity_in_t(o, 2)),
+    "start system derivative d x^(d-1) off by one": (
+        "C<L> dg = cscale<L>(xd1, rfrom<L>((double)H.d[i]));", "C<L> dg = cscale<L>(xd1, rfrom<L>((double)H.d[i] - 1.0));",
+        lambda o: T.test_homotopy_special_cases_and_affinity_in_t(o, 2)),
+    "predictor weights with the wrong sign": (
+        "den = rmul<L>(den, rsub<L>(rfrom<L>(ht[base + j]), rfrom<L>(ht[base + i])));",
+        "den = rmul<L>(den, rsub<L>(rfrom<L>(ht[base + i]), rfrom<L>(ht[base + j])));",
+        lambda o: T.test_predictor_is_exact_on_polynomial_paths(o, 2, 4)),  # (-1)^(m-1): even m
+    "Newton step subtracts the update": (
+        "for (int i = 0; i < n; ++i) x[i] = cadd<L>(x[i], dx[i]);", "for (int i = 0; i < n; ++i) x[i] = csub<L>(x[i], dx[i]);",
+        lambda o: T.test_diagonal_system_closed_form(o, 1)),
+    "divergence test never fires": (
+        "if (norm_inf<L>(x.data(), n) > rdiv_) {", "if (norm_inf<L>(x.data(), n) > 1e300) {",
+        lambda o: T.test_deficient_system_one_root_and_paths_to_infinity(o, 1)),
+    "network forward pass without the first ReLU": (
+        "h1[o] = a > 0 ? a : 0;", "h1[o] = a;",
+        lambda o: N.test_forward_is_a_relu_layer_stack(o)),
+    "network backward pass without the ReLU mask": (
+        "dz2[i] = z2[i] > 0 ? dh2[i] : 0;", "dz2[i] = dh2[i];",
+        lambda o: N.test_gradient_matches_central_differences(o)),
+}
+
+
+def _slug(name):
+    return re.sub(r"[^a-z0-9]+", "_", name.lower()).strip("_")
+
+
+@pytest.fixture(scope="module")
+def mutant_libs(tmp_path_factory):
+    src = oracle.source()
+    d = tmp_path_factory.mktemp("oracle_mutants")
+
+    def build(item):
+        name, (old, new, _) = item
+        assert src.count(old) == 1, name  # the planted line is unambiguous
+        return name, oracle.compile_variant(src.replace(old, new), str(d / (_slug(name) + ".so")))
+
+    with ThreadPoolExecutor(max_workers=max(1, min(len(MUTANTS), os.cpu_count() or 1))) as ex:
+        return dict(ex.map(build, MUTANTS.items()))
+
+
+@pytest.mark.parametrize("name", list(MUTANTS))
+def test_planted_mistake_fails_its_pin(oracle_lib, mutant_libs, name):
+    pin = MUTANTS[name][2]
+    with oracle.loaded_from(mutant_libs[name]):
+        with pytest.raises(AssertionError):
+            pin(oracle)

@@ -5,7 +5,7 @@ import pytest
 
 import synth
 from certify import certify_roots
-from exact import Cx, cx_from, poly_value
+from exact import Cx, cx_from, fr, poly_value
 from fractions import Fraction as Fr
 from match import match_sets, to_complex
 
@@ -160,3 +160,77 @@ def test_deficient_system_one_root_and_paths_to_infinity(oracle_lib, L):
     assert conv.shape[0] == 3 and np.max(np.abs(conv - 1.0)) < 1e-10
     assert certify_roots(s, conv)["distinct_roots"] == 0
     assert certify_roots(s, conv[:1])["distinct_roots"] == 1
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("m", [1, 2, 3, 4, 5])
+def test_predictor_is_exact_on_polynomial_paths(oracle_lib, L, m):
+    """Extrapolation through m points reproduces every path that is a
+    polynomial of degree m - 1 in t: complex polynomials with small integer
+    coefficients at dyadic times, so the data are exact doubles and the
+    expected point is known exactly; the error is rounding only."""
+    from fractions import Fraction as F
+    rng = synth.SplitMix64(900 + 10 * m + L)
+    n = 3
+    ts = [F(k, 16) for k in (0, 2, 3, 5, 6)[:m]]
+    t1 = ts[-1] + F(3, 32)
+    coef = rng.integers(-5, 5, 2 * n * m).reshape(n, 2, m)
+    def p(i, c, t):
+        return sum(F(int(coef[i, c, e])) * t ** e for e in range(m))
+    xs = np.zeros((m, n, 2, L))
+    for j, t in enumerate(ts):
+        for i in range(n):
+            for c in range(2):
+                v = p(i, c, t)
+                xs[j, i, c, 0] = float(v)
+                assert F(xs[j, i, c, 0]) == v  # exact data
+    out = oracle_lib.predict(np.array([float(t) for t in ts]), xs, float(t1))
+    for i in range(n):
+        for c in range(2):
+            err = abs(fr(out[i, c]) - p(i, c, t1))
+            scale = max(1, max(abs(p(i, c, t)) for t in ts))
+            assert err <= 2.0 ** (-53 * L + 12) * scale, (i, c, float(err))
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_homotopy_special_cases_and_affinity_in_t(oracle_lib, L):
+    """h(x, t) = gamma (1 - t) g(x) + t f(x) with g_i = x_i^d_i - 1, checked
+    without restating it: it vanishes at the start solutions at t = 0, where
+    its Jacobian is gamma d_i x_i^(d_i - 1) = gamma d_i conj(x_i) on the
+    diagonal (x_i a root of unity) and zero elsewhere; at t = 1 it is f and
+    f's Jacobian (the pinned evaluation); and h and J are affine in t."""
+    s = synth.config_system("stress_n10_qd")
+    n = s.n_vars
+    deg = s.degrees()
+    gam = synth.random_gamma(4)
+    G = Cx(Fr(gam[0]), Fr(gam[1]))
+    u = 2.0 ** (-53 * L)
+    x0 = oracle_lib.start_solutions(deg, 5, 7, L)
+    h0, J0 = oracle_lib.homotopy(s, deg, gam, 0.0, x0)
+    for q in range(7):
+        for i in range(n):
+            assert cx_from(h0[i, :, :, q]).absf() <= 64 * u
+            for j in range(n):
+                got = cx_from(J0[i, j, :, :, q])
+                if i != j:
+                    assert got.abs2() == 0
+                    continue
+                xi = cx_from(x0[i, :, :, q])
+                want = G * Cx(xi.re, -xi.im) * int(deg[i])
+                assert (got - want).absf() <= 64 * u * int(deg[i])
+    x = synth.unit_points(31 + L, n, 5, L)
+    h1, J1 = oracle_lib.homotopy(s, deg, gam, 1.0, x)
+    fv, fj = oracle_lib.eval_(s, x)
+    assert np.array_equal(h1, fv) and np.array_equal(J1, fj)
+    hz, Jz = oracle_lib.homotopy(s, deg, gam, 0.0, x)
+    t = Fr(3, 8)
+    ht, Jt = oracle_lib.homotopy(s, deg, gam, float(t), x)
+    for q in range(5):
+        for i in range(n):
+            a, b, c = cx_from(hz[i, :, :, q]), cx_from(h1[i, :, :, q]), cx_from(ht[i, :, :, q])
+            want = a * (1 - t) + b * t
+            assert (c - want).absf() <= 2 ** 8 * u * (a.absf() + b.absf() + 1)
+            for j in range(n):
+                a, b, c = (cx_from(Jz[i, j, :, :, q]), cx_from(J1[i, j, :, :, q]), cx_from(Jt[i, j, :, :, q]))
+                want = a * (1 - t) + b * t
+                assert (c - want).absf() <= 2 ** 8 * u * (a.absf() + b.absf() + 1)
