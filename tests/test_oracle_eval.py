@@ -46,6 +46,39 @@ def test_eval_against_exact_brute_force(oracle_lib, L, method):
                 assert (gotd - exd).absf() <= 64 * deg * float(u) * mjac[j, i, p] + 1e-300, (j, i, p)
 
 
+def test_magnitude_scale_is_the_sum_of_term_moduli(oracle_lib):
+    """The tolerance scale sum |term| of each output: with positive real
+    coefficients and positive real points every term is a positive real, so
+    the scale equals the exact value and exact derivative; for complex inputs
+    it bounds the exact value from above (triangle inequality)."""
+    s = _tiny_system(71)
+    rng = synth.SplitMix64(72)
+    pos = synth.System(s.n_vars, s.n_polys, s.n_terms, s.exps,
+                       np.stack([rng.uniform(s.exps.shape[0]) + 0.25, np.zeros(s.exps.shape[0])], 1))
+    x = np.zeros((s.n_vars, 2, 1, 4))
+    x[:, 0, 0, :] = 0.5 + 1.5 * rng.uniform(s.n_vars * 4).reshape(s.n_vars, 4)  # moduli in [0.5, 2)
+    mval, mjac = oracle_lib.eval_magnitude(pos, x)
+    coefs = [Cx(Fr(c[0]), Fr(c[1])) for c in pos.coef]
+    deg = int(pos.exps.astype(int).sum(1).max())
+    for p in range(4):
+        xp = [cx_from(x[i, :, :, p]) for i in range(s.n_vars)]
+        for j in range(s.n_polys):
+            sl = slice(j * 5, (j + 1) * 5)
+            ex = float(poly_value(coefs[sl], pos.exps[sl], xp).re)
+            assert abs(mval[j, p] - ex) <= 1e-13 * ex
+            for i in range(s.n_vars):
+                exd = float(poly_partial_by_interpolation(coefs[sl], pos.exps[sl], xp, i, deg).re)
+                assert abs(mjac[j, i, p] - exd) <= 1e-13 * max(exd, 1e-300)
+    x = synth.unit_points(73, s.n_vars, 4, 1) * 1.7
+    mval, _ = oracle_lib.eval_magnitude(s, x)
+    coefs = [Cx(Fr(c[0]), Fr(c[1])) for c in s.coef]
+    for p in range(4):
+        xp = [cx_from(x[i, :, :, p]) for i in range(s.n_vars)]
+        for j in range(s.n_polys):
+            sl = slice(j * 5, (j + 1) * 5)
+            assert poly_value(coefs[sl], s.exps[sl], xp).absf() <= mval[j, p] * (1 + 1e-13)
+
+
 @pytest.mark.parametrize("L", [1, 2, 4])
 def test_naive_and_reverse_mode_agree(oracle_lib, L):
     """The product rule and the reverse mode are two different computations of

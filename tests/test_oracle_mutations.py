@@ -46,6 +46,15 @@ MUTANTS = {
     "derivative not scaled by the exponent": (
         "C<L> scaled = cscale<L>(cf, rfrom<L>((double)ex[r]));", "C<L> scaled = cf;",
         lambda o: E.test_eval_against_exact_brute_force(o, 1, "speelpenning")),
+    "tolerance scale keeps the differentiated exponent": (
+        "dd *= std::pow(ax[l], (double)(a[l] - (l == i ? 1 : 0)));", "dd *= std::pow(ax[l], (double)(a[l]));",
+        lambda o: E.test_magnitude_scale_is_the_sum_of_term_moduli(o)),
+    "tolerance scale squares the exponent factor": (
+        "double dd = c * a[i];", "double dd = c * a[i] * a[i];",
+        lambda o: E.test_magnitude_scale_is_the_sum_of_term_moduli(o)),
+    "exact difference adds instead of subtracting": (
+        "s.add(-b[i * L + l]);", "s.add(b[i * L + l]);",
+        lambda o: A.test_value_diff_is_exact_difference(o, 2)),
     "Gram-Schmidt projection without the conjugate": (
         "r = cadd<L>(r, cconjmul<L>(M[(size_t)i * W + q], M[(size_t)i * W + j]));",
         "r = cadd<L>(r, cmul<L>(M[(size_t)i * W + q], M[(size_t)i * W + j]));",
