@@ -69,6 +69,18 @@ MUTANTS = {
     "path digits in the wrong radix": (
         "    r /= deg[i];\n", "    r /= 2;\n",
         lambda o: M.test_start_solutions_are_the_roots_of_unity(o, 1, [3, 2])),
+    "roots of unity left at double precision": (
+        "for (int it = 0; it < 3; ++it) {\n      C<L> zd1", "for (int it = 0; it < 0; ++it) {\n      C<L> zd1",
+        lambda o: M.test_start_solutions_are_the_roots_of_unity(o, 2, [5, 3])),
+    "complex division without the conjugate": (
+        "C<L> num = cconjmul<L>(b, a);  // conj(b) a", "C<L> num = cmul<L>(b, a);  // conj(b) a",
+        lambda o: M.test_start_solutions_are_the_roots_of_unity(o, 2, [5, 3])),
+    "start system derivative on the wrong column": (
+        "if (j == i) v = cadd<L>(v, cmul<L>(gs, dg));", "if (j == (i + 1) % n) v = cadd<L>(v, cmul<L>(gs, dg));",
+        lambda o: T.test_homotopy_special_cases_and_affinity_in_t(o, 1)),
+    "Adam without bias correction of the first moment": (
+        "double c1 = 1.0 - std::pow(b1, step)", "double c1 = 1.0",
+        lambda o: N.test_adam_first_step_moves_each_weight_by_lr(o)),
     "compaction keeps finished paths": (
         "if (status[i] == 0) path_idx[c++] = (int32_t)i;", "if (status[i] >= 0) path_idx[c++] = (int32_t)i;",
         lambda o: M.test_compaction_table_tabjobidx(o)),
