@@ -94,6 +94,12 @@ MUTANTS = {
         "den = rmul<L>(den, rsub<L>(rfrom<L>(ht[base + j]), rfrom<L>(ht[base + i])));",
         "den = rmul<L>(den, rsub<L>(rfrom<L>(ht[base + i]), rfrom<L>(ht[base + j])));",
         lambda o: T.test_predictor_is_exact_on_polynomial_paths(o, 2, 4)),  # (-1)^(m-1): even m
+    "step never grows after an accepted step": (
+        "h = std::min(hmax, fup * h);", "h = std::min(hmax, h);",
+        lambda o: T.test_step_control_worked_example(o, 1)),
+    "step grows past its cap": (
+        "h = std::min(hmax, fup * h);", "h = fup * h;",
+        lambda o: T.test_step_control_worked_example(o, 1)),
     "Newton step subtracts the update": (
         "for (int i = 0; i < n; ++i) x[i] = cadd<L>(x[i], dx[i]);", "for (int i = 0; i < n; ++i) x[i] = csub<L>(x[i], dx[i]);",
         lambda o: T.test_diagonal_system_closed_form(o, 1)),

@@ -234,3 +234,20 @@ def test_homotopy_special_cases_and_affinity_in_t(oracle_lib, L):
                 a, b, c = (cx_from(Jz[i, j, :, :, q]), cx_from(J1[i, j, :, :, q]), cx_from(Jt[i, j, :, :, q]))
                 want = a * (1 - t) + b * t
                 assert (c - want).absf() <= 2 ** 8 * u * (a.absf() + b.absf() + 1)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_step_control_worked_example(oracle_lib, L):
+    """g = x - 1, f = 2x - 3 (one variable, degree 1): the homotopy is linear
+    in x, so Newton's method lands on the path in one round and no step is
+    rejected; the step sequence then follows from the step rule alone.  With
+    h0 = 0.05, growth 1.5 and cap 0.1 the accepted steps end at t = 0.05,
+    0.125 (h = 0.075), 0.225, 0.325, ..., 0.925 (h capped at 0.1), and the
+    last step is clamped to t = 1: 11 steps, ending at x = 3/2."""
+    s = synth.System(1, 1, np.array([2], np.int32), np.array([[1], [0]], np.int8),
+                     np.array([[2.0, 0.0], [-3.0, 0.0]]))
+    out = oracle_lib.track(s, [1], synth.random_gamma(8), np.arange(1), L)
+    assert out["status"][0] == 1 and out["t_end"][0] == 1.0
+    assert out["steps"][0] == 11 and out["rejects"][0] == 0
+    z = cx_from(out["x_end"][0, :, :, 0])
+    assert (z - Cx(Fr(3, 2))).absf() <= 4 * 2.0 ** (-53 * L)
