@@ -100,6 +100,15 @@ MUTANTS = {
     "step grows past its cap": (
         "h = std::min(hmax, fup * h);", "h = fup * h;",
         lambda o: T.test_step_control_worked_example(o, 1)),
+    "rejection ignores the shrink factor": (
+        "h = fdown * h;", "h = 0.5 * h;",
+        lambda o: T.test_rejection_worked_example(o, 1, "update")),
+    "acceptance ignores the residual": (
+        "if (ndx <= tol_dx * sx && nres <= lim) {", "if (ndx <= tol_dx * sx) {",
+        lambda o: T.test_rejection_worked_example(o, 1, "residual")),
+    "acceptance ignores the update": (
+        "if (ndx <= tol_dx * sx && nres <= lim) {", "if (nres <= lim) {",
+        lambda o: T.test_rejection_worked_example(o, 1, "update")),
     "Newton step subtracts the update": (
         "for (int i = 0; i < n; ++i) x[i] = cadd<L>(x[i], dx[i]);", "for (int i = 0; i < n; ++i) x[i] = csub<L>(x[i], dx[i]);",
         lambda o: T.test_diagonal_system_closed_form(o, 1)),

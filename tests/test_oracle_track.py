@@ -251,3 +251,34 @@ def test_step_control_worked_example(oracle_lib, L):
     assert out["steps"][0] == 11 and out["rejects"][0] == 0
     z = cx_from(out["x_end"][0, :, :, 0])
     assert (z - Cx(Fr(3, 2))).absf() <= 4 * 2.0 ** (-53 * L)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("case", ["update", "residual"])
+def test_rejection_worked_example(oracle_lib, L, case):
+    """The same linear homotopy with one Newton round per step, cut off by
+    max_steps.  From x = 1 (order-0 prediction) the update is exactly
+    x(t1) - 1 = t1 / (gamma (1 - t1) + 2 t1), of modulus in
+    [t1 / 1.05, t1 / 0.85] for |gamma| = 1 and t1 <= 0.05, and the residual
+    at the predicted point is |h(1, t1)| = t1.  With tol_dx = 0.03:
+      update:   tol_res = 1.  t1 = 0.05 is rejected (update >= 0.047), then
+                h = 0.4 * 0.05 and t1 = 0.02 is accepted: 2 steps, 1 rejection.
+      residual: tol_res = 1e-4.  Every t1 = 0.05 * 0.4^k above 1.0003e-4 fails
+                the residual test; k = 7 (8.19e-5) passes: 8 steps, 7
+                rejections, t = 0.05 * 0.4^7."""
+    s = synth.System(1, 1, np.array([2], np.int32), np.array([[1], [0]], np.int8),
+                     np.array([[2.0, 0.0], [-3.0, 0.0]]))
+    gam = synth.random_gamma(8)
+    tol_res, max_steps, rejects = (1.0, 2, 1) if case == "update" else (1e-4, 8, 7)
+    prm = oracle_lib.default_params(L, newton_max=1, tol_dx=0.03, tol_res=tol_res, f_down=0.4, max_steps=max_steps)
+    out = oracle_lib.track(s, [1], gam, np.arange(1), L, prm)
+    h = 0.05
+    for _ in range(rejects):
+        h = 0.4 * h
+    assert out["status"][0] == -1  # stopped by max_steps
+    assert out["steps"][0] == max_steps and out["rejects"][0] == rejects
+    assert out["t_end"][0] == h
+    t = Fr(h)
+    G = Cx(Fr(gam[0]), Fr(gam[1]))
+    xt = (G * (1 - t) + Cx(3 * t)) / (G * (1 - t) + Cx(2 * t))
+    assert (cx_from(out["x_end"][0, :, :, 0]) - xt).absf() <= 8 * 2.0 ** (-53 * L)
