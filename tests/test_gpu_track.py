@@ -327,6 +327,28 @@ def test_deficient_system_matches_oracle_path_by_path(ht, L, h_max):
     assert np.all(g["t_end"][~conv] > 0.999)  # the others leave near t = 1
 
 
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("case", ["growth", "update", "residual"])
+def test_step_control_worked_examples(ht, L, case):
+    """The step rule on the hand-derived examples of the oracle pins (linear
+    homotopy g = x - 1, f = 2x - 3): 11 accepted steps without rejection;
+    with one Newton round and tol_dx = 0.03, 2 steps with 1 rejection
+    (tol_res = 1) or 8 steps with 7 rejections (tol_res = 1e-4)."""
+    s = synth.System(1, 1, np.array([2], np.int32), np.array([[1], [0]], np.int8),
+                     np.array([[2.0, 0.0], [-3.0, 0.0]]))
+    over, want = {}, (1, 11, 0, 1.0)
+    if case != "growth":
+        tol_res, max_steps, rej = (1.0, 2, 1) if case == "update" else (1e-4, 8, 7)
+        over = dict(newton_max=1, tol_dx=0.03, tol_res=tol_res, f_down=0.4, max_steps=max_steps)
+        h = 0.05
+        for _ in range(rej):
+            h = 0.4 * h
+        want = (-1, max_steps, rej, h)
+    g = track_gpu(ht, s, L, 1, start_deg=[1], gamma=synth.random_gamma(8), **over)
+    got = (int(g["status"][0]), int(g["steps"][0]), int(g["stats"]["rejects"]), float(g["t_end"][0]))
+    assert got == want, (got, want)
+
+
 def test_tracker_rejects_bad_arguments(ht):
     s = synth.config_system("plain_n6_d")
     hs = ht.system_from(s, 1)
