@@ -442,8 +442,10 @@ int ht_step_features(int n, int limbs, int max_order, int newton_max, int64_t n_
  * Same arguments, result and blocking behaviour as ht_compact, except:
  *   - m above HT_NOALLOC_MAX_PATHS is rejected with HT_EINVAL;
  *   - no cudaMalloc, cudaFree or other allocating routine is called;
- *   - the first call on a device looks up the array's device address with that
- *     device current.  Make that first call before any stream capture;
+ *   - every call looks up the array's device address in the current context
+ *     (cudaGetSymbolAddress, which allocates nothing); the first call on a
+ *     device also loads the library's module there, so make it before any
+ *     stream capture;
  *   - all calls share the one array, which keeps the last call's contents.
  *     Each call rewrites all of it that it reads.  Calls whose work overlaps on
  *     the GPU (other streams, other host threads) race on it, so serialise them.

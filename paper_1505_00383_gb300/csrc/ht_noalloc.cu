@@ -2,8 +2,6 @@
 // must not allocate memory (see include/ht.h).  Its only scratch -- the
 // identity index list the compaction reads and the word holding its length --
 // lives in a fixed array in this file instead of a per-call allocation.
-#include <mutex>
-
 #include "ht_internal.h"
 #include "ht_track.h"
 
@@ -21,23 +19,15 @@ __global__ void noalloc_iota_kernel(int32_t* idx, int32_t m) {
   if (blockIdx.x == 0 && threadIdx.x == 0) idx[HT_NOALLOC_MAX_PATHS] = m;
 }
 
-// Device address of the scratch array, looked up once per device with that
-// device current (the host-side symbol is not a device address).
+// Device address of the scratch array in the current context.  The host-side
+// symbol is not a device address; the lookup runs on every call (it allocates
+// nothing), so the address stays right after cudaDeviceReset or when another
+// context of the same device is made current and the module loads again.
 static int noalloc_scratch(int32_t** out) {
-  static std::mutex mu;
-  static int32_t* addr[64] = {nullptr};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return cuda_fail(e, "ht_compact_noalloc: cudaGetDevice");
-  if (dev < 0 || dev >= 64) return set_error(HT_EUNSUPPORTED, "ht_compact_noalloc: device %d", dev);
-  std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, ht_noalloc_scratch);
-    if (e != cudaSuccess) return cuda_fail(e, "ht_compact_noalloc: cudaGetSymbolAddress");
-    addr[dev] = (int32_t*)p;
-  }
-  *out = addr[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, ht_noalloc_scratch);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_compact_noalloc: cudaGetSymbolAddress");
+  *out = (int32_t*)p;
   return HT_OK;
 }
 

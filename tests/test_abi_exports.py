@@ -56,3 +56,15 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "ht_oracle" not in txt, f
+
+
+def test_binding_constants_equal_the_header():
+    """The binding's copies of the header's size constants (the no-alloc
+    scratch limit, the network's shape) cannot drift from include/ht.h."""
+    from paper_1505_00383_gb300 import ht
+    txt = open(os.path.join(ROOT, "include", "ht.h")).read()
+    defs = dict(re.findall(r"^#define\s+(HT_\w+)\s+(.+?)\s*$", txt, flags=re.M))
+    for name in ("HT_NOALLOC_MAX_PATHS", "HT_MLP_IN", "HT_MLP_OUT", "HT_MLP_NPARAM"):
+        expr = defs[name]
+        assert re.fullmatch(r"[0-9()<\s]+", expr), expr
+        assert getattr(ht, name) == eval(expr), name

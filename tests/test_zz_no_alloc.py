@@ -54,3 +54,20 @@ def test_noalloc_rejects_sizes_beyond_its_fixed_scratch(ht):
     with pytest.raises(ht.HTError) as e:
         ht.ht_compact_noalloc(st, ht.HT_NOALLOC_MAX_PATHS + 1, idx, cnt)
     assert e.value.code == ht.HT_EINVAL
+
+
+def test_noalloc_empty_input_writes_only_the_count(ht):
+    """m = 0: status and path_idx may be NULL; only the count (0) is written."""
+    cnt = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+    ht.ht_compact_noalloc(None, 0, None, cnt)
+    assert int(cnt.item()) == 0
+
+
+def test_noalloc_at_its_maximum_size(ht):
+    """m = HT_NOALLOC_MAX_PATHS fills the scratch up to the length word; the
+    result equals the allocating compaction's."""
+    m = ht.HT_NOALLOC_MAX_PATHS
+    st = (synth.SplitMix64(7).integers(0, 3, m) - 1).astype(np.int8)
+    r = _both(ht, st)
+    assert r["noalloc"][0] == r["alloc"][0] == int(np.sum(st == 0))
+    assert np.array_equal(r["noalloc"][1], r["alloc"][1])
