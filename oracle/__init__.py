@@ -15,7 +15,10 @@ Every function follows a passage of Verschelde & Yu (2015):
   * ``track``            the predictor-corrector loop of Section 2;
   * ``real_op``          L-limb arithmetic (double, double double, quad double);
   * ``predict``, ``homotopy``  the tracker's extrapolation predictor and the
-                         homotopy of Eq. eqlinhom with its Jacobian, alone.
+                         homotopy of Eq. eqlinhom with its Jacobian, alone;
+  * ``mlp_*``, ``adam_step``  the learned step-size network (not in the paper):
+                         fp64 forward, loss gradient, Adam, and the error
+                         bound of a reduced-precision evaluation.
 """
 from __future__ import annotations
 
@@ -112,6 +115,7 @@ def _open(path: str):
         "hto_mlp_nparam": ([], i32),
         "hto_mlp_forward": ([i64, P, P, P], i32),
         "hto_mlp_loss_grad": ([i64, P, P, P, P], ctypes.c_double),
+        "hto_mlp_error_bound": ([i64, P, P, P, ctypes.c_double, ctypes.c_double, P, P, P], i32),
         "hto_adam_step": ([i64, P, P, P, P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                            ctypes.c_double, i32], i32),
     }
@@ -309,6 +313,23 @@ def mlp_loss_grad(x, target, params):
     g = np.empty(p.size)
     loss = lib().hto_mlp_loss_grad(x.shape[0], _p(x), _p(t), _p(p), _p(g))
     return float(loss), g
+
+
+def mlp_error_bound(x, target, params, u_act=2.0 ** -8, u_grad=2.0 ** -8):
+    """Rigorous bounds on the distance between the exact network output,
+    loss and gradient (mlp_forward, mlp_loss_grad) and a computation that
+    accumulates in FP32 and rounds the hidden activations (u_act) and the
+    weight-gradient operands (u_grad) to a narrower format: (ybound [B][2],
+    gbound [n_param], loss bound).  The model is stated in ht_oracle.cpp."""
+    x = _c(x, np.float64)
+    t = _c(target, np.float64)
+    p = _c(params, np.float64)
+    yb = np.empty((x.shape[0], MLP_OUT))
+    gb = np.empty(p.size)
+    lb = np.empty(1)
+    assert lib().hto_mlp_error_bound(x.shape[0], _p(x), _p(t), _p(p), float(u_act), float(u_grad), _p(yb), _p(gb),
+                                     _p(lb)) == 0
+    return yb, gb, float(lb[0])
 
 
 def adam_step(p, g, m, v, lr, b1=0.9, b2=0.999, eps=1e-8, step=1):

@@ -1131,6 +1131,148 @@ double hto_mlp_loss_grad(int64_t B, const double* x, const double* target, const
   return loss / (double)B;
 }
 
+// Rigorous bounds on how far a reduced-precision evaluation of the network,
+// its loss and its gradient can lie from the exact values computed above.
+// The model of the reduced-precision side, stated per operation:
+//   * weights and inputs are the same numbers on both sides;
+//   * a dot product of K terms plus a bias is accumulated with error at most
+//     acc (K + 1) |b| + sum |terms|, acc = 2^-23 (FP32 accumulation, products
+//     of the rounded operands exact);
+//   * the hidden activations relu(z) that feed the next layer, and the
+//     weight-gradient operands, are rounded with relative error at most
+//     u_act and u_grad (2^-8 for BF16 with round to nearest);
+//   * the loss derivative 2 (y - t) / B, and the loss, are formed in FP32.
+// Each quantity v of the exact computation gets a bound e_v on the distance
+// of the reduced-precision value, propagated forward in the evaluation order:
+//   |a' b' - a b| <= e_a (|b| + e_b) + |a| e_b,   |relu(a') - relu(a)| <= e_a.
+// Where |z| <= e_z the ReLU mask of the two sides may differ, and the bound
+// of the masked gradient is the whole |gradient| + its own bound.
+// Outputs: ybound [B][2], gbound [MLP_NPARAM], *lbound (loss).
+int hto_mlp_error_bound(int64_t B, const double* x, const double* target, const double* params, double u_act,
+                        double u_grad, double* ybound, double* gbound, double* lbound) {
+  MlpView w(params);
+  const double acc = std::ldexp(1.0, -23), u32 = std::ldexp(1.0, -24);
+  std::memset(gbound, 0, sizeof(double) * MLP_NPARAM);
+  // magnitudes of the gradient sums (for their accumulation error)
+  std::vector<double> gmag(MLP_NPARAM, 0.0);
+  double *eW1 = gbound, *eb1 = eW1 + MH * MI, *eW2 = eb1 + MH, *eb2 = eW2 + MH * MH, *eW3 = eb2 + MH,
+         *eb3 = eW3 + MO * MH;
+  double *mW1 = gmag.data(), *mb1 = mW1 + MH * MI, *mW2 = mb1 + MH, *mb2 = mW2 + MH * MH, *mW3 = mb2 + MH,
+         *mb3 = mW3 + MO * MH;
+  double z1[MH], h1[MH], z2[MH], h2[MH], y[MO];
+  double ez1[MH], eh1[MH], ez2[MH], eh2[MH], ey[MO];
+  double dy[MO], edy[MO], g2[MH], eg2[MH], dz2[MH], edz2[MH], g1[MH], eg1[MH], dz1[MH], edz1[MH];
+  double lmag = 0.0, lerr = 0.0;
+  // rounding of an operand that carries error e: the rounded value differs
+  // from the exact one by at most e + u (|v| + e)
+  auto rnd = [](double v, double e, double u) { return e + u * (std::fabs(v) + e); };
+  for (int64_t b = 0; b < B; ++b) {
+    const double* xb = x + b * MI;
+    mlp_forward_one(w, xb, z1, h1, z2, h2, y);
+    for (int o = 0; o < MH; ++o) {  // layer 1: exact operands, FP32 sum
+      double m = std::fabs(w.b1[o]);
+      for (int i = 0; i < MI; ++i) m += std::fabs(w.W1[o * MI + i] * xb[i]);
+      ez1[o] = acc * (MI + 1) * m;
+      eh1[o] = rnd(h1[o], ez1[o], u_act);
+    }
+    for (int o = 0; o < MH; ++o) {  // layer 2: rounded h1
+      double m = std::fabs(w.b2[o]), e = 0.0;
+      for (int i = 0; i < MH; ++i) {
+        const double a = std::fabs(w.W2[o * MH + i]);
+        e += a * eh1[i];
+        m += a * (h1[i] + eh1[i]);
+      }
+      ez2[o] = e + acc * (MH + 1) * m;
+      eh2[o] = rnd(h2[o], ez2[o], u_act);
+    }
+    for (int o = 0; o < MO; ++o) {  // layer 3: rounded h2
+      double m = std::fabs(w.b3[o]), e = 0.0;
+      for (int i = 0; i < MH; ++i) {
+        const double a = std::fabs(w.W3[o * MH + i]);
+        e += a * eh2[i];
+        m += a * (h2[i] + eh2[i]);
+      }
+      ey[o] = e + acc * (MH + 1) * m;
+      ybound[b * MO + o] = ey[o];
+    }
+    for (int o = 0; o < MO; ++o) {  // loss terms and dL/dy = 2 (y - t) / B (two FP32 roundings)
+      const double r = std::fabs(y[o] - target[b * MO + o]);
+      lerr += 2.0 * r * ey[o] + ey[o] * ey[o];
+      lmag += (r + ey[o]) * (r + ey[o]);
+      dy[o] = 2.0 * (y[o] - target[b * MO + o]) / (double)B;
+      const double ed = 2.0 * ey[o] / (double)B;
+      edy[o] = ed + 2.0 * u32 * (std::fabs(dy[o]) + ed);
+    }
+    for (int i = 0; i < MH; ++i) {  // dh2 = W3^T dy, then the layer-2 mask
+      double v = 0.0, e = 0.0, m = 0.0;
+      for (int o = 0; o < MO; ++o) {
+        const double a = w.W3[o * MH + i];
+        v += a * dy[o];
+        e += std::fabs(a) * edy[o];
+        m += std::fabs(a) * (std::fabs(dy[o]) + edy[o]);
+      }
+      g2[i] = v;
+      eg2[i] = e + acc * (MO + 1) * m;
+      if (z2[i] > ez2[i]) {
+        dz2[i] = g2[i];
+        edz2[i] = eg2[i];
+      } else if (z2[i] < -ez2[i]) {
+        dz2[i] = 0.0;
+        edz2[i] = 0.0;
+      } else {  // the masks may differ
+        dz2[i] = z2[i] > 0 ? g2[i] : 0.0;
+        edz2[i] = std::fabs(g2[i]) + eg2[i];
+      }
+    }
+    for (int i = 0; i < MH; ++i) {  // dh1 = W2^T dz2 with rounded dz2, then the layer-1 mask
+      double v = 0.0, e = 0.0, m = 0.0;
+      for (int o = 0; o < MH; ++o) {
+        const double a = w.W2[o * MH + i];
+        v += a * dz2[o];
+        const double eo = rnd(dz2[o], edz2[o], u_grad);
+        e += std::fabs(a) * eo;
+        m += std::fabs(a) * (std::fabs(dz2[o]) + eo);
+      }
+      g1[i] = v;
+      eg1[i] = e + acc * (MH + 1) * m;
+      if (z1[i] > ez1[i]) {
+        dz1[i] = g1[i];
+        edz1[i] = eg1[i];
+      } else if (z1[i] < -ez1[i]) {
+        dz1[i] = 0.0;
+        edz1[i] = 0.0;
+      } else {
+        dz1[i] = z1[i] > 0 ? g1[i] : 0.0;
+        edz1[i] = std::fabs(g1[i]) + eg1[i];
+      }
+    }
+    // weight gradients: sum over samples of (rounded gradient) x (rounded activation)
+    auto term = [&](double a, double ea, double c, double ec, double* e, double* m) {
+      const double ear = rnd(a, ea, u_grad);
+      *e += ear * (std::fabs(c) + ec) + std::fabs(a) * ec;
+      *m += (std::fabs(a) + ear) * (std::fabs(c) + ec);
+    };
+    for (int o = 0; o < MO; ++o) {
+      eb3[o] += edy[o];
+      mb3[o] += std::fabs(dy[o]) + edy[o];
+      for (int i = 0; i < MH; ++i) term(dy[o], edy[o], h2[i], eh2[i], &eW3[o * MH + i], &mW3[o * MH + i]);
+    }
+    for (int o = 0; o < MH; ++o) {
+      eb2[o] += edz2[o];
+      mb2[o] += std::fabs(dz2[o]) + edz2[o];
+      for (int i = 0; i < MH; ++i) term(dz2[o], edz2[o], h1[i], eh1[i], &eW2[o * MH + i], &mW2[o * MH + i]);
+    }
+    for (int o = 0; o < MH; ++o) {
+      eb1[o] += edz1[o];
+      mb1[o] += std::fabs(dz1[o]) + edz1[o];
+      for (int i = 0; i < MI; ++i) term(dz1[o], edz1[o], xb[i], 0.0, &eW1[o * MI + i], &mW1[o * MI + i]);
+    }
+  }
+  for (int p = 0; p < MLP_NPARAM; ++p) gbound[p] += acc * (double)(B + 1) * gmag[p];
+  *lbound = (lerr + acc * (double)(2 * B + 2) * lmag) / (double)B;
+  return 0;
+}
+
 // One Adam step (Kingma & Ba 2015) on fp64 parameters; step is 1-based.
 int hto_adam_step(int64_t n, double* p, const double* g, double* m, double* v, double lr, double b1, double b2,
                   double eps, int step) {

@@ -115,6 +115,19 @@ MUTANTS = {
     "divergence test never fires": (
         "if (norm_inf<L>(x.data(), n) > rdiv_) {", "if (norm_inf<L>(x.data(), n) > 1e300) {",
         lambda o: T.test_deficient_system_one_root_and_paths_to_infinity(o, 1)),
+    "error bound takes every first-layer ReLU mask as certain": (
+        "        dz1[i] = z1[i] > 0 ? g1[i] : 0.0;\n        edz1[i] = std::fabs(g1[i]) + eg1[i];",
+        "        dz1[i] = z1[i] > 0 ? g1[i] : 0.0;\n        edz1[i] = eg1[i];",
+        lambda o: N.test_error_bound_covers_the_reduced_precision_model(o)),
+    "error bound without the rounding of the hidden activations": (
+        "eh1[o] = rnd(h1[o], ez1[o], u_act);", "eh1[o] = ez1[o];",
+        lambda o: N.test_error_bound_covers_the_reduced_precision_model(o)),
+    "error bound accumulates at the activations' precision": (
+        "const double acc = std::ldexp(1.0, -23), u32", "const double acc = std::ldexp(1.0, -8), u32",
+        lambda o: N.test_error_bound_without_rounding_is_the_accumulation_error(o)),
+    "error bound takes every ReLU mask as uncertain": (
+        "      if (z2[i] > ez2[i]) {", "      if (z2[i] > 1e300) {",
+        lambda o: N.test_error_bound_catches_planted_gradient_mistakes(o)),
     "network forward pass without the first ReLU": (
         "h1[o] = a > 0 ? a : 0;", "h1[o] = a;",
         lambda o: N.test_forward_is_a_relu_layer_stack(o)),
