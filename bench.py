@@ -99,6 +99,8 @@ def _args():
                    help="paths of the held-out n = 16 double system for learned vs plain (0: skip)")
     p.add_argument("--stress", type=int, default=59049,
                    help="paths of the held-out n = 10 quad double system for learned vs plain (0: skip)")
+    p.add_argument("--no-paper-sweep", action="store_true",
+                   help="skip the evaluation sweep of the stand-ins shaped like the paper's applications")
     return p.parse_args()
 
 
@@ -352,6 +354,66 @@ def learned_vs_plain(ht, torch, world, name, m):
     return res
 
 
+# The paper's GPU totals in ms (K20C, Tables tabevalcyclic10, tabevalnash8,
+# tabevalpieri44; evaluation and differentiation at #evals points), for
+# context next to the stand-ins of the same shape: other hardware, other
+# (real) systems.
+PAPER_GPU_MS = {
+    "cyclic10_shape": {"D": {10: 0.028, 1000: 0.282, 3000: 0.826}, "DD": {10: 0.088, 1000: 0.743, 3000: 2.163},
+                       "QD": {10: 0.705, 1000: 5.853, 3000: 16.864}},
+    "nash8_shape": {"D": {10: 0.106, 1000: 1.973, 3000: 5.922}, "DD": {10: 0.361, 1000: 5.341, 3000: 15.922},
+                    "QD": {10: 2.964, 1000: 45.253, 3000: 136.510}},
+    "pieri44_shape": {"D": {10: 0.324, 1000: 6.751, 3000: 20.597}, "DD": {10: 0.995, 1000: 18.299, 3000: 54.879},
+                      "QD": {10: 8.328, 1000: 158.306}},
+}
+
+
+def paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak, reps=10):
+    """ht_eval_diff on the stand-ins shaped like the paper's applications at
+    the point counts of its evaluation tables: per shape and precision the
+    autotuner's choice at 3,000 points, then the median of `reps` launches per
+    point count (CUDA events, L2 flushed before each)."""
+    out = {}
+    for name in ("cyclic10_shape", "nash8_shape", "pieri44_shape"):
+        system = synth.config_system(name)
+        res = {"n": system.n_vars, "monomials": system.n_monomials}
+        for L in PRECISIONS:
+            hs = ht.system_from(system, L)
+            nmax = max(synth.PAPER_SWEEP_POINTS)
+            x = torch.from_numpy(synth.unit_points(900 + L, system.n_vars, nmax, L)).cuda()
+            val = torch.empty((system.n_polys, 2, L, nmax), dtype=torch.float64, device="cuda")
+            jac = torch.empty((system.n_polys, system.n_vars, 2, L, nmax), dtype=torch.float64, device="cuda")
+            v, t, _ = ht.ht_tune_eval(hs, nmax, x, val, jac, reps=3)
+            rows = {}
+            for n in synth.PAPER_SWEEP_POINTS:
+                xs = x[..., :n].contiguous()
+                vs = torch.empty((system.n_polys, 2, L, n), dtype=torch.float64, device="cuda")
+                js = torch.empty((system.n_polys, system.n_vars, 2, L, n), dtype=torch.float64, device="cuda")
+                ht.ht_eval_diff(hs, n, xs, vs, js, stream)
+                ms = []
+                for _ in range(reps):
+                    flush.zero_()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ht.ht_eval_diff(hs, n, xs, vs, js, stream)
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    ms.append(e0.elapsed_time(e1))
+                m = statistics.median(ms)
+                row = {"ms": m, "pts_per_s": n / (m * 1e-3)}
+                if v >= 2:
+                    row["imad_frac"] = int_products_per_point(system, L) * n / (m * 1e-3) / imad_peak
+                else:
+                    row["fp64_frac"] = eval_ops_per_point(system, L) * n / (m * 1e-3) / fp64_peak
+                paper = PAPER_GPU_MS[name][NAMES[L]].get(n)
+                if paper is not None:
+                    row["paper_k20c_ms"] = paper
+                rows[n] = row
+            res[NAMES[L]] = {"variant": VARIANT_NAMES[v], "threads": t, "by_points": rows}
+        out[name] = res
+    return out
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -514,6 +576,10 @@ def run_ours(a):
     if os.path.exists(mp):
         peaks["hbm_GBps_measured"] = json.load(open(mp)).get("hbm_gbs")
 
+    paper_sweep = None
+    if not a.no_paper_sweep:
+        paper_sweep = paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak)
+
     tracking = {}
     oracle_side = rank == 0 and world == 1 and not a.no_cpu
     for name in [w for w in a.track.split(",") if w]:
@@ -548,7 +614,7 @@ def run_ours(a):
                        "monomial_vars": "2-8", "exponents": "1-3", "n_pts_per_gpu": n,
                        "l2": "flushed (512 MB write) before every timed step; outputs 1.1-4.5 GB per launch",
                        "parallelism": "independent batch per GPU"},
-            "per_precision": per_prec, "tuned": tuned, "tracking": tracking, "roofline": roofline, "peaks": peaks, "cpu_baseline": cpu, "e2e": e2e,
+            "per_precision": per_prec, "tuned": tuned, "paper_shapes": paper_sweep, "tracking": tracking, "roofline": roofline, "peaks": peaks, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": a.steps * len(PRECISIONS), "clocks": clk.summary(),
             "wall_s_timed_region": t_wall,
         }))

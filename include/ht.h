@@ -181,12 +181,25 @@ int ht_mlp_forward(const ht_mlp* net, int64_t B, const float* x, float* y, void*
  * [B][2], grad device [HT_MLP_NPARAM] or NULL, loss device [1] or NULL.  Async. */
 int ht_mlp_loss_grad(ht_mlp* net, int64_t B, const float* x, const float* target, float* grad, float* loss,
                      void* stream);
+/* The gradient's products also run on the tensor cores (BF16 operands: the
+ * loss derivative, the activation gradients and the activations; FP32
+ * accumulation).  Per chunk of 64 samples the partial gradients are summed in
+ * a fixed order, so the result depends only on B, x, target and the
+ * parameters. */
 /* Train on n samples (x, target as above, device) for `epochs` passes over
  * consecutive minibatches of `batch` samples (shuffle the data beforehand),
- * one Adam step (beta 0.9 / 0.999, eps 1e-8) per minibatch at rate lr.
+ * one Adam step (as ht_mlp_adam_step) per minibatch at rate lr.
  * epoch_loss: host [epochs] mean minibatch loss per epoch, or NULL.  Blocks. */
 int ht_mlp_train(ht_mlp* net, int64_t n, const float* x, const float* target, int epochs, int64_t batch, float lr,
                  float* epoch_loss, void* stream);
+/* One Adam step (Kingma & Ba 2015: beta1 0.9, beta2 0.999, eps 1e-8, bias
+ * correction by the network's step count, which ht_mlp_set_params resets) on
+ * the FP32 masters with the gradient grad (device [HT_MLP_NPARAM] floats),
+ * then the BF16 copy.  Async. */
+int ht_mlp_adam_step(ht_mlp* net, const float* grad, float lr, void* stream);
+/* Adam's state: first and second moments (host [HT_MLP_NPARAM] floats each,
+ * either may be NULL) and the step count (may be NULL).  Blocks. */
+int ht_mlp_get_moments(const ht_mlp* net, float* m, float* v, int32_t* step);
 
 /* ---------------------------------------------------------------- tracking */
 
@@ -375,6 +388,41 @@ typedef struct ht_track_io {
 int ht_track_paths_ex(ht_system* f, const int32_t* start_deg, const double* gamma, int64_t n_paths,
                       int64_t first_path, const double* x0, const ht_params* p, double* x_end, int8_t* status,
                       double* t_end, int32_t* steps, ht_stats* stats, const ht_track_io* io, void* stream);
+
+/*
+ * ht_track_refined -- mixed-precision tracking, the "quality up" of Sections 1
+ * and 4.4 (the speed of the device spent on accuracy rather than on time):
+ *   1. every path is tracked in the precision of `lo` (ht_track_paths);
+ *   2. every endpoint is refined by Newton's method on f in the precision of
+ *      `hi` (ht_track_paths_ex with polish_only, p_hi->polish_max rounds, x0
+ *      the low-precision endpoints);
+ *   3. every path that failed or diverged in step 1, or whose refinement
+ *      ended non-finite or with its last update above
+ *      p_hi->tol_polish max(1, |x|_inf), is tracked again from its start
+ *      point in the precision of `hi`; its results replace step 2's.
+ * A path tracked again is the high-precision run's path bit for bit; the
+ * others end at the root the low-precision path reached, to the high
+ * precision's accuracy.
+ *   lo, hi     the same system (same monomials) created with fewer limbs
+ *              (lo) and more limbs (hi); both keep workspaces
+ *   start_deg, gamma, n_paths, first_path   as ht_track_paths
+ *   p_lo, p_hi parameters of the two precisions (NULL: ht_default_params)
+ *   x_end      device [n][2][L_hi][n_paths]; status, t_end as ht_track_paths
+ *   rs         host, or NULL: final counts, step-1 converged count, paths
+ *              tracked again, and the wall time of each step
+ * Allocates (stream-ordered) workspaces for the low-precision run and the
+ * selected paths.  Blocks until done.
+ */
+typedef struct ht_refine_stats {
+  int64_t converged, failed, diverged; /* final status 1, -1, -2 */
+  int64_t lo_converged;                /* converged in the low precision */
+  int64_t retracked;                   /* paths tracked again in the high precision */
+  double ms_lo, ms_refine, ms_retrack; /* wall time of steps 1, 2 (with the selection), 3 */
+} ht_refine_stats;
+
+int ht_track_refined(ht_system* lo, ht_system* hi, const int32_t* start_deg, const double* gamma, int64_t n_paths,
+                     int64_t first_path, const ht_params* p_lo, const ht_params* p_hi, double* x_end, int8_t* status,
+                     double* t_end, ht_refine_stats* rs, void* stream);
 
 /*
  * ht_tune_track -- autotuner for ht_track_paths on this system: tracks the

@@ -33,6 +33,7 @@ UNITS = [
     ("ht_track_host.cu", [], "ht_track_host.o"),
     ("ht_noalloc.cu", [], "ht_noalloc.o"),
     ("ht_mlp.cu", [], "ht_mlp.o"),
+    ("ht_refine.cu", [], "ht_refine.o"),
 ]
 
 

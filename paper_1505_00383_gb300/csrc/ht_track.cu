@@ -141,6 +141,38 @@ __device__ __forceinline__ void step_features(float* f, double t, double h, int 
   for (int i = 11; i < FEAT; ++i) f[i] = 0.0f;
 }
 
+// Start points of selected paths: entry q is path first + ids[q].
+template <int L>
+__global__ void start_at_kernel(int n, const int32_t* __restrict__ deg, int64_t first, const int32_t* __restrict__ ids,
+                                const int32_t* __restrict__ count, double* __restrict__ x, int64_t ld) {
+  const int64_t cnt = *count;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * blockDim.x) {
+    int64_t r = first + ids[q];
+    for (int i = 0; i < n; ++i) {
+      int d = __ldg(deg + i);
+      int k = (int)(r % d);
+      r /= d;
+      st<L>(x, i, ld, q, root_of_unity<L>(d, k));
+    }
+  }
+}
+
+// Results of selected paths into the full arrays: path ids[q] of dst takes
+// entry q of src (points [n][2][L][ld_src] and [n][2][L][m]).
+template <int L>
+__global__ void scatter_kernel(int n, const int32_t* __restrict__ ids, const int32_t* __restrict__ count,
+                               const double* __restrict__ xs, const int8_t* __restrict__ ss,
+                               const double* __restrict__ ts, int64_t ld_src, double* __restrict__ xd,
+                               int8_t* __restrict__ sd, double* __restrict__ td, int64_t m) {
+  const int64_t cnt = *count;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < cnt; q += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = ids[q];
+    for (int i = 0; i < n; ++i) st<L>(xd, i, m, p, ld<L>(xs, i, ld_src, q));
+    sd[p] = ss[q];
+    td[p] = ts[q];
+  }
+}
+
 template <int L>
 __global__ void features_kernel(const double* __restrict__ rec, int64_t n_rec, int n, int cap, int newton_max,
                                 float* __restrict__ feat) {
@@ -884,6 +916,28 @@ int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_
 }
 
 template <int L>
+int launch_start_at_l(int n, const int32_t* d_deg, int64_t first, const int32_t* ids, const int32_t* count,
+                      int64_t cap, double* x, cudaStream_t st) {
+  if (cap == 0) return HT_OK;
+  int64_t blocks = (cap + 127) / 128;
+  if (blocks > 4096) blocks = 4096;
+  start_at_kernel<L><<<(unsigned)blocks, 128, 0, st>>>(n, d_deg, first, ids, count, x, cap);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "start points launch");
+}
+
+template <int L>
+int launch_scatter_l(int n, const int32_t* ids, const int32_t* count, int64_t cap, const double* xs, const int8_t* ss,
+                     const double* ts, double* xd, int8_t* sd, double* td, int64_t m, cudaStream_t st) {
+  if (cap == 0) return HT_OK;
+  int64_t blocks = (cap + 127) / 128;
+  if (blocks > 4096) blocks = 4096;
+  scatter_kernel<L><<<(unsigned)blocks, 128, 0, st>>>(n, ids, count, xs, ss, ts, cap, xd, sd, td, m);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? HT_OK : cuda_fail(e, "scatter launch");
+}
+
+template <int L>
 int launch_features_l(const double* rec, int64_t n_rec, int n, int cap, int newton_max, float* feat, cudaStream_t st) {
   if (n_rec == 0) return HT_OK;
   int64_t blocks = (n_rec + 127) / 128;
@@ -909,5 +963,9 @@ template int launch_init_l<HT_LIMBS>(const TrackArgs&, cudaStream_t);
 template int launch_track_l<HT_LIMBS>(const TrackArgs&, int, int64_t, cudaStream_t);
 template int track_occupancy_l<HT_LIMBS>(int);
 template int launch_features_l<HT_LIMBS>(const double*, int64_t, int, int, int, float*, cudaStream_t);
+template int launch_start_at_l<HT_LIMBS>(int, const int32_t*, int64_t, const int32_t*, const int32_t*, int64_t, double*,
+                                         cudaStream_t);
+template int launch_scatter_l<HT_LIMBS>(int, const int32_t*, const int32_t*, int64_t, const double*, const int8_t*,
+                                        const double*, double*, int8_t*, double*, int64_t, cudaStream_t);
 
 }  // namespace ht

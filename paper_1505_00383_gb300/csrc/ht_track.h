@@ -95,6 +95,14 @@ template <int L>
 int track_occupancy_l(int team);
 template <int L>
 int launch_features_l(const double* rec, int64_t n_rec, int n, int cap, int newton_max, float* feat, cudaStream_t st);
+// Start points of paths first + ids[q] for q < *count (x: [n][2][L][cap]).
+template <int L>
+int launch_start_at_l(int n, const int32_t* d_deg, int64_t first, const int32_t* ids, const int32_t* count,
+                      int64_t cap, double* x, cudaStream_t st);
+// Entry q of (xs [n][2][L][cap], ss, ts) into path ids[q] of (xd [n][2][L][m], sd, td), q < *count.
+template <int L>
+int launch_scatter_l(int n, const int32_t* ids, const int32_t* count, int64_t cap, const double* xs, const int8_t* ss,
+                     const double* ts, double* xd, int8_t* sd, double* td, int64_t m, cudaStream_t st);
 int launch_mlp_image(void* img, const __nv_bfloat16* wbf, const float* master, cudaStream_t st);
 size_t mlp_image_bytes();
 int launch_compact(const int32_t* idx_in, const int32_t* count_in, const int8_t* status, int32_t* idx_out,

@@ -40,6 +40,8 @@ SIGNATURES = {
     "ht_mlp_forward": ([P, I64, P, P, P], I32),
     "ht_mlp_loss_grad": ([P, I64, P, P, P, P, P], I32),
     "ht_mlp_train": ([P, I64, P, P, I32, I64, ctypes.c_float, P, P], I32),
+    "ht_mlp_adam_step": ([P, P, ctypes.c_float, P], I32),
+    "ht_mlp_get_moments": ([P, P, P, P], I32),
     "ht_default_params": ([I32, P], I32),
     "ht_start_solutions": ([I32, P, I32, I64, I64, P, P], I32),
     "ht_mgs_solve": ([I32, I32, I32, I64, P, P, P, P], I32),
@@ -48,6 +50,7 @@ SIGNATURES = {
     "ht_compact_noalloc": ([P, I64, P, P, P], I32),
     "ht_track_paths": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P], I32),
     "ht_track_paths_ex": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P, P], I32),
+    "ht_track_refined": ([P, P, P, P, I64, I64, P, P, P, P, P, P, P], I32),
     "ht_tune_track": ([P, P, P, I64, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_double), P], I32),
     "ht_record_size": ([I32, I32, I32], I64),
@@ -77,6 +80,14 @@ class ht_track_io(ctypes.Structure):
 class ht_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("converged", "failed", "diverged", "steps", "rejects", "newton")] + \
                [("launches", ctypes.c_int32), ("syncs", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ht_refine_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_int64) for k in ("converged", "failed", "diverged", "lo_converged", "retracked")] + \
+               [(k, ctypes.c_double) for k in ("ms_lo", "ms_refine", "ms_retrack")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -271,6 +282,20 @@ def ht_track_paths(sys: System, start_deg, gamma, n_paths, first_path, x0, param
                                 _ptr(status), _ptr(t_end), _ptr(steps), sp, _stream(stream)))
 
 
+def ht_track_refined(lo: System, hi: System, start_deg, gamma, n_paths, first_path, p_lo, p_hi, x_end, status,
+                     t_end, stats: "ht_refine_stats | None" = None, stream=None) -> None:
+    """Track in lo's precision, refine endpoints in hi's, track failures again
+    in hi's; device outputs x_end [n][2][L_hi][n_paths], status, t_end."""
+    import numpy as np
+    d = np.ascontiguousarray(start_deg, dtype=np.int32)
+    g = np.ascontiguousarray(gamma, dtype=np.float64)
+    pl = None if p_lo is None else ctypes.byref(p_lo)
+    ph = None if p_hi is None else ctypes.byref(p_hi)
+    sp = None if stats is None else ctypes.byref(stats)
+    _check(lib().ht_track_refined(lo.handle, hi.handle, _ptr(d), _ptr(g), n_paths, first_path, pl, ph, _ptr(x_end),
+                                  _ptr(status), _ptr(t_end), sp, _stream(stream)))
+
+
 HT_MLP_IN, HT_MLP_OUT, HT_MLP_NPARAM = 16, 2, 5378
 
 
@@ -326,6 +351,21 @@ def ht_mlp_train(net: Mlp, n, x, target, epochs, batch, lr, stream=None):
     _check(lib().ht_mlp_train(net.handle, n, _ptr(x), _ptr(target), epochs, batch, ctypes.c_float(lr), _ptr(losses),
                               _stream(stream)))
     return losses
+
+
+def ht_mlp_adam_step(net: Mlp, grad, lr, stream=None) -> None:
+    """One Adam step on the network's FP32 masters with a device gradient."""
+    _check(lib().ht_mlp_adam_step(net.handle, _ptr(grad), ctypes.c_float(lr), _stream(stream)))
+
+
+def ht_mlp_get_moments(net: Mlp):
+    """(m, v, step): Adam's moments (float32 arrays) and step count."""
+    import numpy as np
+    m = np.empty(HT_MLP_NPARAM, dtype=np.float32)
+    v = np.empty(HT_MLP_NPARAM, dtype=np.float32)
+    step = ctypes.c_int32(0)
+    _check(lib().ht_mlp_get_moments(net.handle, _ptr(m), _ptr(v), ctypes.byref(step)))
+    return m, v, int(step.value)
 
 
 def ht_record_size(n, limbs, max_order=4) -> int:

@@ -21,7 +21,8 @@ path index fastest):
   number (1 = double, 2 = double double, 4 = quad double), limb 0 the leading one.
 
 The workload shapes follow the paper's synthetic benchmark families; see
-``CONFIGS`` for the five families and their seeds.
+``CONFIGS`` for the five workload families, the three stand-ins shaped like
+the paper's benchmark applications, and their seeds.
 """
 from __future__ import annotations
 
@@ -257,6 +258,65 @@ def extreme_system(seed: int, n_vars: int, n_polys: int) -> System:
                   meta={"seed": seed, "family": "extreme"})
 
 
+def _multilinear(rng: SplitMix64, n: int, k: int) -> tuple[int, ...]:
+    """An exponent vector with k distinct variables, each to the power 1."""
+    a = [0] * n
+    for v in rng.choice_without_replacement(n, k).tolist():
+        a[v] = 1
+    return tuple(a)
+
+
+def paper_shaped_system(kind: str, seed: int) -> System:
+    """Random systems with the shapes the paper reports for its three benchmark
+    applications (Section 4.2, Table tabsumchar): the dimension, the number of
+    monomials of each polynomial and their degrees.  The monomials are drawn
+    at random (products of distinct variables, exponent 1: the paper gives
+    degrees, not exponents); coefficients are uniform on the unit circle.
+
+    * "cyclic10": 10 variables; polynomial k = 1..9 has 10 distinct monomials
+      of degree k; the last has one monomial of degree 10 and a constant
+      (92 monomials);
+    * "nash8": 8 variables, 8 polynomials of 130 distinct monomials whose
+      degrees are uniform in 1..7 (1,040 monomials);
+    * "pieri44": 16 variables, 16 polynomials of 246 distinct monomials of
+      degree 4 (3,936 monomials).
+    """
+    rng = SplitMix64(seed)
+    polys: list[list[tuple[int, ...]]] = []
+    if kind == "cyclic10":
+        n = 10
+        for k in range(1, n):
+            seen: list[tuple[int, ...]] = []
+            while len(seen) < 10:
+                a = _multilinear(rng, n, k)
+                if a not in seen:
+                    seen.append(a)
+            polys.append(seen)
+        polys.append([tuple([1] * n), tuple([0] * n)])
+    elif kind in ("nash8", "pieri44"):
+        n, per, kmin, kmax = (8, 130, 1, 7) if kind == "nash8" else (16, 246, 4, 4)
+        for _ in range(n):
+            seen = []
+            have = set()
+            while len(seen) < per:
+                k = int(rng.integers(kmin, kmax, 1)[0])
+                a = _multilinear(rng, n, k)
+                if a not in have:
+                    have.add(a)
+                    seen.append(a)
+            polys.append(seen)
+    else:
+        raise ValueError("unknown paper shape %r" % kind)
+    exps = np.array([a for p in polys for a in p], dtype=np.int8)
+    M = exps.shape[0]
+    re, im = unit_circle(rng, M)
+    return System(
+        n_vars=n, n_polys=n, n_terms=np.array([len(p) for p in polys], dtype=np.int32), exps=exps,
+        coef=np.ascontiguousarray(np.stack([re, im], axis=1)),
+        meta={"seed": seed, "family": "paper_shape", "kind": kind},
+    )
+
+
 def unit_points(seed: int, n_vars: int, n_pts: int, limbs: int) -> np.ndarray:
     """Points with |x_i| = 1 (to rounding in limb 0) and uniform phase; lower
     limbs are random non-overlapping tails.  Shape [n_vars][2][limbs][n_pts]."""
@@ -283,12 +343,23 @@ CONFIGS = {
     "learned_n16_d": dict(kind="track", n=16, degree=2, n_monomials=24, limbs=1, seed=3000,
                          train_seeds=(3000, 3200), heldout_seeds=(3500, 3520)),
     "stress_n10_qd": dict(kind="track", n=10, degree=3, n_monomials=32, limbs=4, seed=4000),
+    # stand-ins with the shapes of the paper's benchmark applications (Table
+    # tabsumchar), for evaluation sweeps over 10..3000 points
+    "cyclic10_shape": dict(kind="paper_shape", shape="cyclic10", n=10, monomials=92, seed=5000),
+    "nash8_shape": dict(kind="paper_shape", shape="nash8", n=8, monomials=1040, seed=6000),
+    "pieri44_shape": dict(kind="paper_shape", shape="pieri44", n=16, monomials=3936, seed=7000),
 }
+
+# numbers of points of the paper's evaluation tables (Tables tabevalcyclic10,
+# tabevalnash8, tabevalpieri44)
+PAPER_SWEEP_POINTS = (10, 20, 50, 100, 200, 500, 1000, 2000, 3000)
 
 
 def config_system(name: str, seed: int | None = None) -> System:
     c = CONFIGS[name]
     s = c["seed"] if seed is None else seed
+    if c["kind"] == "paper_shape":
+        return paper_shaped_system(c["shape"], s)
     if c["kind"] == "evaldiff":
         return sparse_support_system(s, c["n_vars"], c["n_polys"], c["n_monomials"],
                                      c["k_min"], c["k_max"], c["e_min"], c["e_max"])

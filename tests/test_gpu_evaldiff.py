@@ -268,3 +268,28 @@ def test_maximum_sizes_255_variables(ht, L):
     jac = torch.full((s.n_polys, 255, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
     ht.ht_eval_diff(hs, n, xd, val, jac)
     assert np.array_equal(val.cpu().numpy(), a[0]) and np.array_equal(jac.cpu().numpy(), a[1])
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("name", ["cyclic10_shape", "nash8_shape", "pieri44_shape"])
+def test_paper_shaped_systems_match_oracle(ht, name, variant, L):
+    """The stand-ins shaped like the paper's three applications (Section 4.2,
+    Table tabsumchar), at the largest point count of its evaluation tables
+    (3,000 points) on sampled points, and at the smallest (10 points) on all,
+    with the FP64 bodies (variant 1) and the integer limbs (variant 2)."""
+    s = synth.config_system(name)
+    for n, sample in ((3000, {1: 12, 2: 6, 4: 3}[L]), (10, None)):
+        x = synth.unit_points(500 + L + n, s.n_vars, n, L)
+        hs = ht.system_from(s, L)
+        ht.ht_set_eval_config(hs, variant, 256 if variant == 2 else 0)
+        xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        val = torch.full((s.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+        jac = torch.full((s.n_polys, s.n_vars, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+        ht.ht_eval_diff(hs, n, xd, val, jac)
+        torch.cuda.synchronize()
+        pts = None
+        if sample is not None:
+            rng = synth.SplitMix64(77 + L)
+            pts = np.unique(np.concatenate([[0, 31, n - 1], rng.integers(0, n - 1, sample)]))
+        _check(s, x, L, val.cpu().numpy(), jac.cpu().numpy(), pts=pts)

@@ -463,3 +463,50 @@ def test_track_autotuner_picks_a_valid_shape_and_keeps_results(ht):
         torch.cuda.synchronize()
         out.append((x.cpu().numpy(), st.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0], equal_nan=True) and np.array_equal(out[0][1], out[1][1])
+
+
+def _golden_track(name):
+    import sys
+    sys.path.insert(0, GOLDEN)
+    import make_track_oracle as M
+    d = np.load(M.path(name))
+    return M, {k: d[k] for k in d.files}
+
+
+@pytest.mark.parametrize("name", ["batched_n12_dd", "stress_n10_qd"])
+def test_full_workload_matches_oracle_on_1024_sampled_paths(ht, name):
+    """All paths of the workload (4,096 DD; 59,049 QD) tracked at once in the
+    launch shape the benchmark times (DD: the built-in shape; QD: the
+    autotuner's choice on 1,024 paths), against the oracle's one-by-one
+    tracking of 1,024 seeded path indices (tests/golden, written by a script
+    that calls only the oracle): the same status for every sampled path and
+    the same endpoint to 1e-10 relative to max(1, |x|_inf)."""
+    M, gold = _golden_track(name)
+    L, h_min = M.CASES[name][0], M.CASES[name][1]
+    cfg = synth.CONFIGS[name]
+    s = synth.config_system(name)
+    gam = synth.random_gamma(cfg["seed"])
+    m = cfg["degree"] ** cfg["n"]
+    hs = ht.system_from(s, L)
+    prm = ht.ht_default_params(L, h_min=h_min)
+    if name == "stress_n10_qd":
+        team, iters, _ = ht.ht_tune_track(hs, s.degrees(), gam, 1024, prm)
+        prm.team_warps, prm.iters_per_launch = team, iters
+    n = s.n_vars
+    x = torch.full((n, 2, L, m), np.nan, dtype=torch.float64, device="cuda")
+    st = torch.full((m,), 9, dtype=torch.int8, device="cuda")
+    t = torch.full((m,), np.nan, dtype=torch.float64, device="cuda")
+    ht.ht_track_paths(hs, s.degrees(), gam, m, 0, None, prm, x, st, t, None, None)
+    torch.cuda.synchronize()
+    ids = gold["ids"]
+    assert ids.size == 1024 and ids[0] == 0 and ids[-1] == m - 1
+    sg = st.cpu().numpy()[ids]
+    assert np.array_equal(sg, gold["status"]), np.flatnonzero(sg != gold["status"])[:10]
+    conv = gold["status"] == 1
+    xg = x.cpu().numpy()[:, :, 0, :][..., ids]
+    zg = (xg[:, 0] + 1j * xg[:, 1]).T[conv]
+    zo = (gold["x_lead"][:, 0] + 1j * gold["x_lead"][:, 1]).T[conv]
+    scale = np.maximum(1.0, np.max(np.abs(zo), axis=1))
+    err = np.max(np.maximum(np.abs(zg.real - zo.real), np.abs(zg.imag - zo.imag)), axis=1) / scale
+    assert np.all(err <= 1e-10), (np.max(err), ids[conv][np.argmax(err)])
+    assert np.all(t.cpu().numpy()[ids][conv] == 1.0)
