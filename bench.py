@@ -99,6 +99,10 @@ def _args():
                    help="paths of the held-out n = 16 double system for learned vs plain (0: skip)")
     p.add_argument("--stress", type=int, default=59049,
                    help="paths of the held-out n = 10 quad double system for learned vs plain (0: skip)")
+    p.add_argument("--no-ablation", action="store_true",
+                   help="skip the three-kernel (coeff, mon, sum) evaluation against the fused kernel")
+    p.add_argument("--no-quality-up", action="store_true",
+                   help="skip the mixed-precision (double tracking, double double refinement) comparison")
     p.add_argument("--no-paper-sweep", action="store_true",
                    help="skip the evaluation sweep of the stand-ins shaped like the paper's applications")
     return p.parse_args()
@@ -267,6 +271,94 @@ def _agreement(A, B, tol=1e-10):
         scale = np.maximum(1.0, np.max(np.abs(P), axis=1))
         fr.append(float(np.mean(d <= tol * scale)))
     return min(fr)
+
+
+def unfused_ablation(ht, torch, stream, flush, system, xs, n, fused_ms):
+    """The paper's three-kernel organisation (coeff, mon, sum over a vertical
+    workspace; Section 3, Tables tabcpugpu and tabmemory) against the fused
+    kernel on the same points: per precision one timed call after a warm-up,
+    each kernel's time and its algorithmic bandwidth (Table tabbench reports
+    the mon and sum kernels' GB/s on the K20C)."""
+    out = {}
+    for L in PRECISIONS:
+        hs = ht.system_from(system, L)
+        ht.ht_set_eval_config(hs, 1, 0)
+        val = torch.empty((system.n_polys, 2, L, n), dtype=torch.float64, device="cuda")
+        jac = torch.empty((system.n_polys, system.n_vars, 2, L, n), dtype=torch.float64, device="cuda")
+        ht.ht_eval_diff_unfused(hs, n, xs[L], val, jac, None, stream)  # workspace, term lists
+        flush.zero_()
+        st = ht.ht_unfused_stats()
+        ht.ht_eval_diff_unfused(hs, n, xs[L], val, jac, st, stream)
+        d = st.as_dict()
+        tot = d["ms_coeff"] + d["ms_mon"] + d["ms_sum"]
+        out[NAMES[L]] = {
+            "ms": {"coeff": d["ms_coeff"], "mon": d["ms_mon"], "sum": d["ms_sum"], "total": tot},
+            "GB_per_s": {k: d["bytes_" + k] / (d["ms_" + k] * 1e-3) / 1e9 for k in ("coeff", "mon", "sum")},
+            "workspace_GB_moved": (d["bytes_coeff"] + d["bytes_mon"] + d["bytes_sum"]) / 1e9,
+            "fused_ms": fused_ms[L], "fused_variant": "the benchmark's tuned kernel",
+            "unfused_over_fused": tot / fused_ms[L]}
+        del val, jac
+    return out
+
+
+def quality_up(ht, torch, world, name="batched_n12_dd", Lh=2, h_min=1e-6):
+    """Accuracy against time (the paper's "quality up"): the workload tracked
+    in double alone, in double with refinement in the high precision and the
+    failures tracked again there (ht_track_refined), and in the high
+    precision alone.  Accuracy of each arm: the largest distance of its
+    converged endpoints to the high-precision run's (leading two limbs,
+    nearest-neighbour pairing)."""
+    from scipy.spatial import cKDTree
+    s = synth.config_system(name)
+    gam = synth.random_gamma(synth.CONFIGS[name]["seed"])
+    m = int(np.prod(s.degrees().astype(np.int64)))
+    n = s.n_vars
+    lo, hi = ht.system_from(s, 1), ht.system_from(s, Lh)
+    pl, ph = ht.ht_default_params(1, h_min=h_min), ht.ht_default_params(Lh, h_min=h_min)
+    bufs = lambda L: (torch.empty((n, 2, L, m), dtype=torch.float64, device="cuda"),
+                      torch.empty((m,), dtype=torch.int8, device="cuda"),
+                      torch.empty((m,), dtype=torch.float64, device="cuda"))
+    xd, sd, td = bufs(1)
+    xr, sr, tr = bufs(Lh)
+    xh, sh, th = bufs(Lh)
+    rs = ht.ht_refine_stats()
+    arms = {"d_only": lambda: ht.ht_track_paths(lo, s.degrees(), gam, m, 0, None, pl, xd, sd, td),
+            "refined": lambda: ht.ht_track_refined(lo, hi, s.degrees(), gam, m, 0, pl, ph, xr, sr, tr, rs),
+            "high_only": lambda: ht.ht_track_paths(hi, s.degrees(), gam, m, 0, None, ph, xh, sh, th)}
+    sec = {}
+    for k, f in arms.items():
+        f()  # warm-up: workspaces and graphs
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        f()
+        torch.cuda.synchronize()
+        sec[k] = time.perf_counter() - t0
+
+    def lead2(x):
+        x = x.cpu().numpy()
+        z = x[:, 0, 0, :] + 1j * x[:, 1, 0, :]
+        if x.shape[2] > 1:
+            z = z + (x[:, 0, 1, :] + 1j * x[:, 1, 1, :])
+        return z.T
+
+    ref = lead2(xh)[sh.cpu().numpy() == 1]
+    tree = cKDTree(np.concatenate([ref.real, ref.imag], axis=1))
+
+    def dist(x, st):
+        z = lead2(x)[st.cpu().numpy() == 1]
+        d, _ = tree.query(np.concatenate([z.real, z.imag], axis=1), k=1, p=np.inf)
+        return float(np.max(d / np.maximum(1.0, np.max(np.abs(z), axis=1)))) if z.size else None
+
+    count = lambda st: {c: int((st.cpu().numpy() == v).sum()) for c, v in (("converged", 1), ("failed", -1),
+                                                                             ("diverged", -2))}
+    return {"paths": m, "n": n, "high": NAMES[Lh],
+            "seconds": sec, "paths_per_s": {k: world * m / v for k, v in sec.items()},
+            "refined_phases_ms": {k: rs.as_dict()[k] for k in ("ms_lo", "ms_refine", "ms_retrack")},
+            "retracked": rs.retracked,
+            "counts": {"d_only": count(sd), "refined": count(sr), "high_only": count(sh)},
+            "max_dist_to_high_run": {"d_only": dist(xd, sd), "refined": dist(xr, sr)},
+            "what": "double tracking; double + refinement in %s + failures re-tracked in %s; %s alone"
+                    % (NAMES[Lh], NAMES[Lh], NAMES[Lh])}
 
 
 # learned+batched against plain batched: the workload, its tracking and check
@@ -576,6 +668,10 @@ def run_ours(a):
     if os.path.exists(mp):
         peaks["hbm_GBps_measured"] = json.load(open(mp)).get("hbm_gbs")
 
+    ablation = None
+    if not a.no_ablation:
+        ablation = unfused_ablation(ht, torch, stream, flush, system, xs, n,
+                                    {L: statistics.mean(launch_ms[L]) for L in PRECISIONS})
     paper_sweep = None
     if not a.no_paper_sweep:
         paper_sweep = paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak)
@@ -589,6 +685,8 @@ def run_ours(a):
             tracking[name]["cpu_baseline"] = oracle_track_rate(name, cfg["seed"], TRACK_LIMBS[name],
                                                                0.01 if name == "plain_n6_d" else 1e-6,
                                                                ORACLE_TRACK_SAMPLE[name])
+    if not a.no_quality_up:
+        tracking["quality_up_n12_dd"] = quality_up(ht, torch, world)
     for name, m, key in (("learned_n16_d", a.learned, "learned_n16_d_vs_plain"),
                          ("stress_n10_qd", a.stress, "stress_n10_qd_vs_plain")):
         if m > 0:
@@ -614,7 +712,7 @@ def run_ours(a):
                        "monomial_vars": "2-8", "exponents": "1-3", "n_pts_per_gpu": n,
                        "l2": "flushed (512 MB write) before every timed step; outputs 1.1-4.5 GB per launch",
                        "parallelism": "independent batch per GPU"},
-            "per_precision": per_prec, "tuned": tuned, "paper_shapes": paper_sweep, "tracking": tracking, "roofline": roofline, "peaks": peaks, "cpu_baseline": cpu, "e2e": e2e,
+            "per_precision": per_prec, "tuned": tuned, "unfused_ablation": ablation, "paper_shapes": paper_sweep, "tracking": tracking, "roofline": roofline, "peaks": peaks, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": a.steps * len(PRECISIONS), "clocks": clk.summary(),
             "wall_s_timed_region": t_wall,
         }))

@@ -110,6 +110,36 @@ int ht_eval_diff(const ht_system* sys, int64_t n_pts, const double* x, double* v
 int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, double* val_host,
                       double* jac_host, void* stream);
 
+/*
+ * ht_eval_diff_unfused -- ht_eval_diff organised as the paper's three kernels
+ * (Section 3, Tables tabcpugpu and tabmemory), kept as an ablation of the
+ * fused kernel and for bandwidth measurements like Table tabbench:
+ *   coeff  writes the coefficient of every monomial at every point to a
+ *          workspace in device memory;
+ *   mon    evaluates every monomial and its derivatives at every point by the
+ *          reverse mode of Table tabmoneval and writes them to the workspace;
+ *   sum    adds every polynomial's terms and every Jacobian entry's terms
+ *          (in monomial order) into val and jac.
+ * The workspace rows are vertical (point fastest), so every access is
+ * coalesced.  The operations and their order are those of ht_eval_diff's
+ * FP64 bodies (variants 0 and 1), so the results are bitwise identical to
+ * theirs.  Points go in chunks whose workspace fits in 2 GiB; the workspace
+ * and the sum kernel's term lists are built on first use and kept in the
+ * system.  Up to 65,535 monomials and n_polys (n_vars + 1) <= 65,535.
+ *   x, val, jac  device, as ht_eval_diff
+ *   stats        host, or NULL; when given, each kernel is timed with CUDA
+ *                events on `stream` (the call then blocks) and its
+ *                algorithmic bytes (every workspace row written or read once,
+ *                16 L bytes per complex entry) are summed over the chunks
+ */
+typedef struct ht_unfused_stats {
+  double ms_coeff, ms_mon, ms_sum;          /* kernel times, summed over chunks */
+  double bytes_coeff, bytes_mon, bytes_sum; /* algorithmic bytes moved by each kernel */
+} ht_unfused_stats;
+
+int ht_eval_diff_unfused(ht_system* sys, int64_t n_pts, const double* x, double* val, double* jac,
+                         ht_unfused_stats* stats, void* stream);
+
 /* ------------------------------------------------------------ tuning */
 
 /*

@@ -34,6 +34,9 @@ UNITS = [
     ("ht_noalloc.cu", [], "ht_noalloc.o"),
     ("ht_mlp.cu", [], "ht_mlp.o"),
     ("ht_refine.cu", [], "ht_refine.o"),
+    ("ht_unfused.cu", ["-DHT_LIMBS=1"], "ht_unfused_1.o"),
+    ("ht_unfused.cu", ["-DHT_LIMBS=2"], "ht_unfused_2.o"),
+    ("ht_unfused.cu", ["-DHT_LIMBS=4"], "ht_unfused_4.o"),
 ]
 
 

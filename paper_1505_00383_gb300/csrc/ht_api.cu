@@ -196,6 +196,8 @@ int ht_destroy_system(ht_system* s) {
   if (s->d_ws) cudaFree(s->d_ws);
   if (s->d_track_ws) cudaFree(s->d_track_ws);
   if (s->d_coef_fz) cudaFree(s->d_coef_fz);
+  if (s->d_uf) cudaFree(s->d_uf);
+  if (s->d_uf_ws) cudaFree(s->d_uf_ws);
   if (s->h_count) cudaFreeHost(s->h_count);
   for (auto& hs : s->host_streams)
     if (hs) cudaStreamDestroy(hs);

@@ -43,6 +43,13 @@ struct ht_system {
     cudaGraphExec_t exec = nullptr;
   };
   std::vector<GraphEntry> graphs;
+  // three-kernel evaluation (ht_eval_diff_unfused): the output lists of the
+  // sum kernel and the workspace, built on first use
+  void* d_uf = nullptr;          // out_off [np (nv + 1) + 1] | out_slot [T] | out_exp [T] | slot_off [M + 1] (int32)
+  int64_t uf_slots = 0;          // workspace entries per point: M (coefficients) + sum over monomials of k + 1
+  int64_t uf_terms = 0;          // T: summands over all outputs
+  void* d_uf_ws = nullptr;
+  size_t uf_ws_bytes = 0;
 };
 
 namespace ht {
@@ -58,5 +65,12 @@ template <int L>
 int launch_evaldiff_l(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st);
 int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac,
                     cudaStream_t st);
+
+// The three kernels of ht_eval_diff_unfused on points p0 .. p0 + cc - 1 of
+// x/val/jac (column stride n) through the workspace ws ([slots][2][L][cc]);
+// with ev (6 events) the kernels are bracketed for timing.
+template <int L>
+int launch_unfused_l(const ht_system* s, int64_t n, int64_t p0, int64_t cc, const double* x, double* val,
+                     double* jac, double* ws, cudaEvent_t* ev, cudaStream_t st);
 
 }  // namespace ht

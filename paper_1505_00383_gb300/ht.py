@@ -51,6 +51,7 @@ SIGNATURES = {
     "ht_track_paths": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P], I32),
     "ht_track_paths_ex": ([P, P, P, I64, I64, P, P, P, P, P, P, P, P, P], I32),
     "ht_track_refined": ([P, P, P, P, I64, I64, P, P, P, P, P, P, P], I32),
+    "ht_eval_diff_unfused": ([P, I64, P, P, P, P, P], I32),
     "ht_tune_track": ([P, P, P, I64, P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(ctypes.c_double), P], I32),
     "ht_record_size": ([I32, I32, I32], I64),
@@ -80,6 +81,14 @@ class ht_track_io(ctypes.Structure):
 class ht_stats(ctypes.Structure):
     _fields_ = [(k, ctypes.c_int64) for k in ("converged", "failed", "diverged", "steps", "rejects", "newton")] + \
                [("launches", ctypes.c_int32), ("syncs", ctypes.c_int32), ("ms", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ht_unfused_stats(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_double) for k in ("ms_coeff", "ms_mon", "ms_sum", "bytes_coeff", "bytes_mon",
+                                                "bytes_sum")]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -280,6 +289,14 @@ def ht_track_paths(sys: System, start_deg, gamma, n_paths, first_path, x0, param
     sp = None if stats is None else ctypes.byref(stats)
     _check(lib().ht_track_paths(sys.handle, _ptr(d), _ptr(g), n_paths, first_path, _ptr(x0), pp, _ptr(x_end),
                                 _ptr(status), _ptr(t_end), _ptr(steps), sp, _stream(stream)))
+
+
+def ht_eval_diff_unfused(sys: System, n_pts, x, val, jac, stats: "ht_unfused_stats | None" = None,
+                         stream=None) -> None:
+    """The three-kernel (coeff, mon, sum) evaluation; stats (optional) times
+    each kernel and counts its algorithmic bytes."""
+    sp = None if stats is None else ctypes.byref(stats)
+    _check(lib().ht_eval_diff_unfused(sys.handle, n_pts, _ptr(x), _ptr(val), _ptr(jac), sp, _stream(stream)))
 
 
 def ht_track_refined(lo: System, hi: System, start_deg, gamma, n_paths, first_path, p_lo, p_hi, x_end, status,

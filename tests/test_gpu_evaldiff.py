@@ -293,3 +293,52 @@ def test_paper_shaped_systems_match_oracle(ht, name, variant, L):
             rng = synth.SplitMix64(77 + L)
             pts = np.unique(np.concatenate([[0, 31, n - 1], rng.integers(0, n - 1, sample)]))
         _check(s, x, L, val.cpu().numpy(), jac.cpu().numpy(), pts=pts)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("name", ["evaldiff_n32", "cyclic10_shape", "nash8_shape", "stress_n10_qd"])
+def test_unfused_three_kernels_equal_the_fused_kernel(ht, name, L):
+    """The paper's coeff / mon / sum organisation over a device workspace
+    (ht_eval_diff_unfused) takes the fused FP64 bodies' operations in their
+    order: bitwise the same values and Jacobian, on three warps of points and
+    a ragged tail; and within the oracle's tolerance."""
+    s = synth.config_system(name)
+    n = 32 * 3 + 5
+    x = synth.unit_points(211 + L, s.n_vars, n, L)
+    hs = ht.system_from(s, L)
+    ht.ht_set_eval_config(hs, 1, 0)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    out = []
+    for unfused in (False, True):
+        val = torch.full((s.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+        jac = torch.full((s.n_polys, s.n_vars, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+        if unfused:
+            st = ht.ht_unfused_stats()
+            ht.ht_eval_diff_unfused(hs, n, xd, val, jac, st)
+            d = st.as_dict()
+            assert d["ms_mon"] > 0 and d["bytes_mon"] > d["bytes_coeff"] > 0 and d["bytes_sum"] > 0
+        else:
+            ht.ht_eval_diff(hs, n, xd, val, jac)
+        torch.cuda.synchronize()
+        out.append((val.cpu().numpy(), jac.cpu().numpy()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    _check(s, x, L, out[1][0], out[1][1])
+
+
+def test_unfused_in_chunks_at_full_size(ht):
+    """65,536 points in QD need several workspace chunks: sampled points of
+    the last chunks against the fused kernel, bit for bit."""
+    s = synth.config_system("evaldiff_n32")
+    n, L = 65536, 4
+    x = torch.from_numpy(synth.unit_points(1004, s.n_vars, n, L)).cuda()
+    hs = ht.system_from(s, L)
+    ht.ht_set_eval_config(hs, 1, 0)
+    res = []
+    for unfused in (False, True):
+        val = torch.full((s.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+        jac = torch.full((s.n_polys, s.n_vars, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+        (ht.ht_eval_diff_unfused if unfused else ht.ht_eval_diff)(hs, n, x, val, jac)
+        torch.cuda.synchronize()
+        pts = torch.tensor([0, 2047, 2048, 40000, n - 1], device="cuda")
+        res.append((val[..., pts].cpu().numpy(), jac[..., pts].cpu().numpy()))
+    assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])
