@@ -16,6 +16,8 @@ Every function follows a passage of Verschelde & Yu (2015):
   * ``real_op``          L-limb arithmetic (double, double double, quad double);
   * ``predict``, ``homotopy``  the tracker's extrapolation predictor and the
                          homotopy of Eq. eqlinhom with its Jacobian, alone;
+  * ``tangent``, ``predict_tangent``  the path tangent from J v = -dh/dt and
+                         the Euler and Hermite predictors built on it;
   * ``mlp_*``, ``adam_step``  the learned step-size network (not in the paper):
                          fp64 forward, loss gradient, Adam, and the error
                          bound of a reduced-precision evaluation.
@@ -38,7 +40,7 @@ _lib = None
 
 # Tracker parameters, in the order the C side reads them.
 PARAM_NAMES = ("h0", "h_min", "h_max", "f_up", "f_down", "newton_max", "tol_dx", "tol_res",
-               "polish_max", "tol_polish", "r_div", "max_steps", "max_order")
+               "polish_max", "tol_polish", "r_div", "max_steps", "max_order", "predictor")
 
 
 def build(force: bool = False) -> str:
@@ -112,6 +114,9 @@ def _open(path: str):
         "hto_track": ([i32, i32, P, P, P, P, P, i64, P, P, i32, P, P, P, P, P, P], i32),
         "hto_predict": ([i32, i32, i32, P, P, ctypes.c_double, P], i32),
         "hto_homotopy": ([i32, i32, P, P, P, P, P, ctypes.c_double, i64, P, P, P], i32),
+        "hto_tangent": ([i32, i32, P, P, P, P, P, ctypes.c_double, i64, P, P], i32),
+        "hto_predict_tangent": ([i32, i32, i32, ctypes.c_double, P, P, ctypes.c_double, P, P, ctypes.c_double, P],
+                                i32),
         "hto_mlp_nparam": ([], i32),
         "hto_mlp_forward": ([i64, P, P, P], i32),
         "hto_mlp_loss_grad": ([i64, P, P, P, P], ctypes.c_double),
@@ -237,7 +242,7 @@ def default_params(limbs: int, **over) -> dict:
     used by both the oracle and the CUDA library)."""
     p = dict(h0=0.05, h_min=1e-5, h_max=0.1, f_up=1.5, f_down=0.5, newton_max=3, tol_dx=1e-6, tol_res=1e-4,
              polish_max=4, tol_polish={1: 1e-12, 2: 1e-24, 4: 1e-48}[limbs], r_div=1e8, max_steps=2000,
-             max_order=4)
+             max_order=4, predictor=0)
     p.update(over)
     return p
 
@@ -286,6 +291,34 @@ def homotopy(system, start_degrees, gamma, t: float, x: np.ndarray):
     J = np.empty((n, n, 2, L, n_pts))
     assert lib().hto_homotopy(L, n, _p(nt), _p(ex), _p(cf), _p(d), _p(g), float(t), n_pts, _p(x), _p(h), _p(J)) == 0
     return h, J
+
+
+def tangent(system, start_degrees, gamma, t: float, x: np.ndarray) -> np.ndarray:
+    """The path tangent dx/dt of Eq. eqlinhom at points x [n][2][L][n_pts] and
+    time t, from J_x v = -dh/dt by the Newton step's least squares."""
+    x = _c(x, np.float64)
+    n, _, L, n_pts = x.shape
+    nt, ex, cf = _sys_args(system, L)
+    d = _c(start_degrees, np.int32)
+    g = _c(np.array(gamma, dtype=np.float64), np.float64)
+    v = np.empty_like(x)
+    assert lib().hto_tangent(L, n, _p(nt), _p(ex), _p(cf), _p(d), _p(g), float(t), n_pts, _p(x), _p(v)) == 0
+    return v
+
+
+def predict_tangent(mode: int, s0, x0, v0, s1, x1, v1, t1) -> np.ndarray:
+    """The tracker's tangent predictors (points [n][2][L]): mode 1 Euler from
+    (s1, x1, v1), mode 2 the cubic Hermite through (s0, x0, v0), (s1, x1, v1)."""
+    x1 = _c(x1, np.float64)
+    n, _, L = x1.shape
+    z = np.zeros_like(x1)
+    x0 = z if x0 is None else _c(x0, np.float64)
+    v0 = z if v0 is None else _c(v0, np.float64)
+    v1 = _c(v1, np.float64)
+    out = np.empty_like(x1)
+    assert lib().hto_predict_tangent(L, n, mode, float(s0), _p(x0), _p(v0), float(s1), _p(x1), _p(v1), float(t1),
+                                     _p(out)) == 0
+    return out
 
 
 # ------------------------------------------------------------------ learned step

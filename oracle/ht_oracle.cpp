@@ -471,15 +471,16 @@ void eval_magnitude(const Sys<L>& s, const C<L>* x, double* val, double* jac) {
 }
 
 // ---------------------------------------------------------- least squares
-// Modified Gram-Schmidt on the augmented matrix [A | b] (rows >= cols), then
-// back substitution R x = Q^H b.  A is row major [rows][cols].
+// Modified Gram-Schmidt on the augmented matrix [A | b_0 .. b_{nrhs-1}]
+// (rows >= cols), then back substitution R x_k = Q^H b_k for every right-hand
+// side.  A is row major [rows][cols], b is [nrhs][rows], x is [nrhs][cols].
 template <int L>
-void mgs_solve(int rows, int cols, std::vector<C<L>>& A, std::vector<C<L>>& b, C<L>* x) {
-  const int W = cols + 1;
+void mgs_solve_multi(int rows, int cols, int nrhs, const std::vector<C<L>>& A, const C<L>* b, C<L>* x) {
+  const int W = cols + nrhs;
   std::vector<C<L>> M((size_t)rows * W);
   for (int i = 0; i < rows; ++i) {
     for (int j = 0; j < cols; ++j) M[(size_t)i * W + j] = A[(size_t)i * cols + j];
-    M[(size_t)i * W + cols] = b[i];
+    for (int k = 0; k < nrhs; ++k) M[(size_t)i * W + cols + k] = b[(size_t)k * rows + i];
   }
   std::vector<C<L>> Rm((size_t)cols * W, czero<L>());
   for (int q = 0; q < cols; ++q) {
@@ -499,12 +500,19 @@ void mgs_solve(int rows, int cols, std::vector<C<L>>& A, std::vector<C<L>>& b, C
         M[(size_t)i * W + j] = csub<L>(M[(size_t)i * W + j], cmul<L>(r, M[(size_t)i * W + q]));
     }
   }
-  for (int q = cols - 1; q >= 0; --q) {
-    C<L> acc = Rm[(size_t)q * W + cols];
-    for (int j = q + 1; j < cols; ++j) acc = csub<L>(acc, cmul<L>(Rm[(size_t)q * W + j], x[j]));
-    R<L> rqq = Rm[(size_t)q * W + q].re;
-    x[q] = C<L>{rdiv<L>(acc.re, rqq), rdiv<L>(acc.im, rqq)};
+  for (int k = 0; k < nrhs; ++k) {
+    C<L>* xk = x + (size_t)k * cols;
+    for (int q = cols - 1; q >= 0; --q) {
+      C<L> acc = Rm[(size_t)q * W + cols + k];
+      for (int j = q + 1; j < cols; ++j) acc = csub<L>(acc, cmul<L>(Rm[(size_t)q * W + j], xk[j]));
+      R<L> rqq = Rm[(size_t)q * W + q].re;
+      xk[q] = C<L>{rdiv<L>(acc.re, rqq), rdiv<L>(acc.im, rqq)};
+    }
   }
+}
+template <int L>
+void mgs_solve(int rows, int cols, std::vector<C<L>>& A, std::vector<C<L>>& b, C<L>* x) {
+  mgs_solve_multi<L>(rows, cols, 1, A, b.data(), x);
 }
 
 // ---------------------------------------------------------- start solutions
@@ -558,7 +566,7 @@ void start_solution(int n, const int32_t* deg, int64_t path, C<L>* x) {
 // Parameters, in this order, as doubles (Section 2 leaves all of them open):
 enum {
   P_H0, P_HMIN, P_HMAX, P_FUP, P_FDOWN, P_NEWTON_MAX, P_TOL_DX, P_TOL_RES,
-  P_POLISH_MAX, P_TOL_POLISH, P_RDIV, P_MAX_STEPS, P_MAX_ORDER, P_COUNT
+  P_POLISH_MAX, P_TOL_POLISH, P_RDIV, P_MAX_STEPS, P_MAX_ORDER, P_PREDICTOR, P_COUNT
 };
 
 template <int L>
@@ -569,9 +577,10 @@ struct Homotopy {
   int deg_max;
 };
 
-// h(x, t) = gamma (1 - t) g(x) + t f(x)  (Eq. eqlinhom) and its Jacobian in x.
+// h(x, t) = gamma (1 - t) g(x) + t f(x)  (Eq. eqlinhom), its Jacobian in x,
+// and (ht != nullptr) its derivative in t, f(x) - gamma g(x).
 template <int L>
-void eval_homotopy(const Homotopy<L>& H, const C<L>* x, double t, C<L>* h, C<L>* J) {
+void eval_homotopy(const Homotopy<L>& H, const C<L>* x, double t, C<L>* h, C<L>* J, C<L>* ht = nullptr) {
   const int n = H.f.nv;
   std::vector<C<L>> fv(n), fj((size_t)n * n);
   eval_speel<L>(H.f, x, fv.data(), fj.data());
@@ -583,6 +592,7 @@ void eval_homotopy(const Homotopy<L>& H, const C<L>* x, double t, C<L>* h, C<L>*
     C<L> g = csub<L>(cmul<L>(xd1, x[i]), C<L>{rfrom<L>(1.0), rzero<L>()});
     C<L> dg = cscale<L>(xd1, rfrom<L>((double)H.d[i]));
     h[i] = cadd<L>(cmul<L>(gs, g), cscale<L>(fv[i], tt));
+    if (ht) ht[i] = csub<L>(fv[i], cmul<L>(H.gamma, g));
     for (int j = 0; j < n; ++j) {
       C<L> v = cscale<L>(fj[(size_t)i * n + j], tt);
       if (j == i) v = cadd<L>(v, cmul<L>(gs, dg));
@@ -605,14 +615,22 @@ bool all_finite(const C<L>* v, int n) {
 }
 
 // One Newton step at (x, t): x <- x + dx with J dx = -h by least squares.
-// Returns |dx|_inf and |h|_inf (at x before the update).
+// Returns |dx|_inf and |h|_inf (at x before the update).  With tan !=
+// nullptr the same factorisation also solves J v = -dh/dt, the tangent of the
+// path (Section 2's predictor stage): v is written to tan.
 template <int L>
-void newton_step(const Homotopy<L>& H, std::vector<C<L>>& x, double t, double* ndx, double* nres) {
+void newton_step(const Homotopy<L>& H, std::vector<C<L>>& x, double t, double* ndx, double* nres,
+                 std::vector<C<L>>* tan = nullptr) {
   const int n = H.f.nv;
-  std::vector<C<L>> h(n), J((size_t)n * n), rhs(n), dx(n);
-  eval_homotopy<L>(H, x.data(), t, h.data(), J.data());
+  const int nrhs = tan ? 2 : 1;
+  std::vector<C<L>> h(n), J((size_t)n * n), rhs((size_t)nrhs * n), sol((size_t)nrhs * n), dht(n);
+  eval_homotopy<L>(H, x.data(), t, h.data(), J.data(), tan ? dht.data() : nullptr);
   for (int i = 0; i < n; ++i) rhs[i] = C<L>{rneg<L>(h[i].re), rneg<L>(h[i].im)};
-  mgs_solve<L>(n, n, J, rhs, dx.data());
+  if (tan)
+    for (int i = 0; i < n; ++i) rhs[n + i] = C<L>{rneg<L>(dht[i].re), rneg<L>(dht[i].im)};
+  mgs_solve_multi<L>(n, n, nrhs, J, rhs.data(), sol.data());
+  std::vector<C<L>> dx(sol.begin(), sol.begin() + n);
+  if (tan) tan->assign(sol.begin() + n, sol.end());
   for (int i = 0; i < n; ++i) x[i] = cadd<L>(x[i], dx[i]);
   *ndx = norm_inf<L>(dx.data(), n);
   *nres = norm_inf<L>(h.data(), n);
@@ -643,6 +661,39 @@ void predict(const std::vector<double>& ht, const std::vector<std::vector<C<L>>>
   }
 }
 
+// Predictors from tangents (Section 2's predictor stage, with the tangent
+// v = dx/dt of the path from J v = -dh/dt):
+//   Euler    x(t1) = x1 + (t1 - s1) v1 through the current point (s1, x1, v1);
+//   Hermite  the cubic that matches (s0, x0, v0) and (s1, x1, v1), evaluated
+//            at t1: with d = s1 - s0 and u = (t1 - s0) / d,
+//            x(t1) = (2u^3 - 3u^2 + 1) x0 + (u^3 - 2u^2 + u) d v0
+//                  + (-2u^3 + 3u^2) x1 + (u^3 - u^2) d v1.
+template <int L>
+void predict_euler(double s1, const std::vector<C<L>>& x1, const std::vector<C<L>>& v1, double t1,
+                   std::vector<C<L>>& out) {
+  R<L> dt = rsub<L>(rfrom<L>(t1), rfrom<L>(s1));
+  for (size_t c = 0; c < out.size(); ++c) out[c] = cadd<L>(x1[c], cscale<L>(v1[c], dt));
+}
+template <int L>
+void predict_hermite(double s0, const std::vector<C<L>>& x0, const std::vector<C<L>>& v0, double s1,
+                     const std::vector<C<L>>& x1, const std::vector<C<L>>& v1, double t1, std::vector<C<L>>& out) {
+  const R<L> d = rsub<L>(rfrom<L>(s1), rfrom<L>(s0));
+  const R<L> u = rdiv<L>(rsub<L>(rfrom<L>(t1), rfrom<L>(s0)), d);
+  const R<L> u2 = rmul<L>(u, u), u3 = rmul<L>(u2, u);
+  const R<L> one = rfrom<L>(1.0), two = rfrom<L>(2.0), three = rfrom<L>(3.0);
+  const R<L> a0 = radd<L>(rsub<L>(rmul<L>(two, u3), rmul<L>(three, u2)), one);
+  const R<L> b0 = rmul<L>(radd<L>(rsub<L>(u3, rmul<L>(two, u2)), u), d);
+  const R<L> a1 = rsub<L>(rmul<L>(three, u2), rmul<L>(two, u3));
+  const R<L> b1 = rmul<L>(rsub<L>(u3, u2), d);
+  for (size_t c = 0; c < out.size(); ++c) {
+    C<L> acc = cscale<L>(x0[c], a0);
+    acc = cadd<L>(acc, cscale<L>(v0[c], b0));
+    acc = cadd<L>(acc, cscale<L>(x1[c], a1));
+    acc = cadd<L>(acc, cscale<L>(v1[c], b1));
+    out[c] = acc;
+  }
+}
+
 struct PathResult {
   int8_t status;
   double t;
@@ -659,21 +710,36 @@ PathResult track_one(const Homotopy<L>& H, const double* P, std::vector<C<L>>& x
   const int max_steps = (int)P[P_MAX_STEPS], max_order = (int)P[P_MAX_ORDER];
   const double tol_dx = P[P_TOL_DX], tol_res = P[P_TOL_RES], tol_polish = P[P_TOL_POLISH];
   const double rdiv_ = P[P_RDIV];
+  // predictor: 0 extrapolation through up to max_order + 1 accepted points;
+  // 1 Euler on the tangent of the current point; 2 cubic Hermite on the
+  // current and the previous point and their tangents.  The start point has
+  // no tangent: until one exists the extrapolation predictor of order 0
+  // (Euler: also until then; Hermite: Euler with one tangent).
+  const int pmode = (int)P[P_PREDICTOR];
 
   std::vector<double> ht{0.0};
   std::vector<std::vector<C<L>>> hx{x};
+  std::vector<std::vector<C<L>>> hv{std::vector<C<L>>()};  // tangents (empty: none)
   double t = 0.0, h = h0;
   PathResult res{0, 0.0, 0, 0, 0};
-  std::vector<C<L>> xp(n);
+  std::vector<C<L>> xp(n), tan_last;
   while (res.status == 0) {
     double step = std::min(h, 1.0 - t);
     double t1 = (step >= 1.0 - t) ? 1.0 : t + step;
-    int m = std::min<int>((int)ht.size(), max_order + 1);
-    predict<L>(ht, hx, m, t1, xp);
+    const size_t nh = ht.size();
+    const bool v1 = !hv[nh - 1].empty(), v0 = nh >= 2 && !hv[nh - 2].empty();
+    if (pmode == 2 && v1 && v0) {
+      predict_hermite<L>(ht[nh - 2], hx[nh - 2], hv[nh - 2], ht[nh - 1], hx[nh - 1], hv[nh - 1], t1, xp);
+    } else if (pmode >= 1 && v1) {
+      predict_euler<L>(ht[nh - 1], hx[nh - 1], hv[nh - 1], t1, xp);
+    } else {
+      int m = std::min<int>((int)ht.size(), pmode >= 1 ? 1 : max_order + 1);
+      predict<L>(ht, hx, m, t1, xp);
+    }
     bool ok = false;
     for (int it = 0; it < newton_max; ++it) {
       double ndx, nres;
-      newton_step<L>(H, xp, t1, &ndx, &nres);
+      newton_step<L>(H, xp, t1, &ndx, &nres, pmode >= 1 ? &tan_last : nullptr);
       ++res.newton;
       if (!(ndx == ndx)) break;  // NaN: reject
       double sx = std::max(1.0, norm_inf<L>(xp.data(), n));
@@ -690,9 +756,11 @@ PathResult track_one(const Homotopy<L>& H, const double* P, std::vector<C<L>>& x
       x = xp;
       ht.push_back(t);
       hx.push_back(x);
+      hv.push_back(pmode >= 1 ? tan_last : std::vector<C<L>>());
       if ((int)ht.size() > max_order + 1) {
         ht.erase(ht.begin());
         hx.erase(hx.begin());
+        hv.erase(hv.begin());
       }
       h = std::min(hmax, fup * h);
       if (norm_inf<L>(x.data(), n) > rdiv_) {
@@ -913,6 +981,53 @@ int homotopy_points(int n, const int32_t* n_terms, const int8_t* exps, const dou
   return 0;
 }
 
+// The path tangent at points x [n][2][L][n_pts] and time t: v solves
+// J_x v = -dh/dt by the least squares of the Newton step (out [n][2][L][n_pts]).
+template <int L>
+int tangent_points(int n, const int32_t* n_terms, const int8_t* exps, const double* coef, const int32_t* start_deg,
+                   const double* gamma, double t, int64_t n_pts, const double* x, double* v) {
+  Homotopy<L> H;
+  H.f = make_sys<L>(n, n, n_terms, exps, coef);
+  H.d.assign(start_deg, start_deg + n);
+  H.gamma = C<L>{rfrom<L>(gamma[0]), rfrom<L>(gamma[1])};
+  H.deg_max = H.f.max_deg;
+  std::vector<C<L>> xv(n), tv;
+  for (int64_t p = 0; p < n_pts; ++p) {
+    for (int i = 0; i < n; ++i) xv[i] = load_soa<L>(x, i, p, n_pts);
+    double ndx, nres;
+    newton_step<L>(H, xv, t, &ndx, &nres, &tv);
+    for (int i = 0; i < n; ++i) store_soa<L>(v, i, p, n_pts, tv[i]);
+  }
+  return 0;
+}
+
+// The tangent predictors alone: mode 1 Euler from (s1, x1, v1), mode 2 cubic
+// Hermite from (s0, x0, v0) and (s1, x1, v1); points [n][2][L].
+template <int L>
+int predict_tangent_one(int n, int mode, double s0, const double* x0, const double* v0, double s1, const double* x1,
+                        const double* v1, double t1, double* out) {
+  auto load = [&](const double* a) {
+    std::vector<C<L>> z(n);
+    for (int i = 0; i < n; ++i)
+      for (int l = 0; l < L; ++l) {
+        z[i].re.v[l] = a[(i * 2 + 0) * L + l];
+        z[i].im.v[l] = a[(i * 2 + 1) * L + l];
+      }
+    return z;
+  };
+  std::vector<C<L>> o(n);
+  if (mode == 1)
+    predict_euler<L>(s1, load(x1), load(v1), t1, o);
+  else
+    predict_hermite<L>(s0, load(x0), load(v0), s1, load(x1), load(v1), t1, o);
+  for (int i = 0; i < n; ++i)
+    for (int l = 0; l < L; ++l) {
+      out[(i * 2 + 0) * L + l] = o[i].re.v[l];
+      out[(i * 2 + 1) * L + l] = o[i].im.v[l];
+    }
+  return 0;
+}
+
 }  // namespace
 
 template <template <int> class F, typename... A>
@@ -931,6 +1046,8 @@ template <int L> struct StartF { template <typename... A> static int run(A... a)
 template <int L> struct TrackF { template <typename... A> static int run(A... a) { return track_batch<L>(a...); } };
 template <int L> struct PredF { template <typename... A> static int run(A... a) { return predict_one<L>(a...); } };
 template <int L> struct HomF { template <typename... A> static int run(A... a) { return homotopy_points<L>(a...); } };
+template <int L> struct TanF { template <typename... A> static int run(A... a) { return tangent_points<L>(a...); } };
+template <int L> struct PTanF { template <typename... A> static int run(A... a) { return predict_tangent_one<L>(a...); } };
 template <int L>
 struct SlotsF {
   static int run(int k, const double* x, double* slots) {
@@ -1046,6 +1163,21 @@ int hto_homotopy(int L, int n, const int32_t* n_terms, const int8_t* exps, const
                  const int32_t* start_deg, const double* gamma, double t, int64_t n_pts, const double* x, double* h,
                  double* J) {
   return dispatch_l<HomF>(L, n, n_terms, exps, coef, start_deg, gamma, t, n_pts, x, h, J);
+}
+
+// The path tangent v = dx/dt of Eq. eqlinhom at points x [n][2][L][n_pts] and
+// time t, from J_x v = -dh/dt (v [n][2][L][n_pts]).
+int hto_tangent(int L, int n, const int32_t* n_terms, const int8_t* exps, const double* coef,
+                const int32_t* start_deg, const double* gamma, double t, int64_t n_pts, const double* x, double* v) {
+  return dispatch_l<TanF>(L, n, n_terms, exps, coef, start_deg, gamma, t, n_pts, x, v);
+}
+
+// The tracker's tangent predictors: mode 1 Euler, 2 cubic Hermite (points
+// [n][2][L]; mode 1 reads only s1, x1, v1).
+int hto_predict_tangent(int L, int n, int mode, double s0, const double* x0, const double* v0, double s1,
+                        const double* x1, const double* v1, double t1, double* out) {
+  if (n < 1 || (mode != 1 && mode != 2)) return -1;
+  return dispatch_l<PTanF>(L, n, mode, s0, x0, v0, s1, x1, v1, t1, out);
 }
 
 // Start solutions of x_i^d_i - 1 = 0 for paths first..first+count-1:

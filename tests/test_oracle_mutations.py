@@ -60,8 +60,8 @@ MUTANTS = {
         "r = cadd<L>(r, cmul<L>(M[(size_t)i * W + q], M[(size_t)i * W + j]));",
         lambda o: M.test_mgs_matches_lstsq_in_double(o, 6, 6)),
     "back substitution adds instead of subtracting": (
-        "acc = csub<L>(acc, cmul<L>(Rm[(size_t)q * W + j], x[j]));",
-        "acc = cadd<L>(acc, cmul<L>(Rm[(size_t)q * W + j], x[j]));",
+        "acc = csub<L>(acc, cmul<L>(Rm[(size_t)q * W + j], xk[j]));",
+        "acc = cadd<L>(acc, cmul<L>(Rm[(size_t)q * W + j], xk[j]));",
         lambda o: M.test_mgs_matches_lstsq_in_double(o, 6, 6)),
     "roots of unity at half the angle": (
         "double th = 2.0 * pi * (double)k / (double)d;", "double th = pi * (double)k / (double)d;",
@@ -128,6 +128,16 @@ MUTANTS = {
     "error bound takes every ReLU mask as uncertain": (
         "      if (z2[i] > ez2[i]) {", "      if (z2[i] > 1e300) {",
         lambda o: N.test_error_bound_catches_planted_gradient_mistakes(o)),
+    "tangent with the sign of dh/dt flipped": (
+        "if (ht) ht[i] = csub<L>(fv[i], cmul<L>(H.gamma, g));", "if (ht) ht[i] = cadd<L>(fv[i], cmul<L>(H.gamma, g));",
+        lambda o: T.test_tangent_of_the_diagonal_system_in_closed_form(o, 1)),
+    "back substitution solves the first right-hand side twice": (
+        "C<L> acc = Rm[(size_t)q * W + cols + k];", "C<L> acc = Rm[(size_t)q * W + cols];",
+        lambda o: T.test_tangent_of_the_diagonal_system_in_closed_form(o, 2)),
+    "Hermite predictor forgets to scale the first tangent by the interval": (
+        "const R<L> b0 = rmul<L>(radd<L>(rsub<L>(u3, rmul<L>(two, u2)), u), d);",
+        "const R<L> b0 = radd<L>(rsub<L>(u3, rmul<L>(two, u2)), u);",
+        lambda o: T.test_tangent_predictors_are_exact_on_polynomial_paths(o, 1)),
     "network forward pass without the first ReLU": (
         "h1[o] = a > 0 ? a : 0;", "h1[o] = a;",
         lambda o: N.test_forward_is_a_relu_layer_stack(o)),

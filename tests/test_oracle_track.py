@@ -282,3 +282,135 @@ def test_rejection_worked_example(oracle_lib, L, case):
     G = Cx(Fr(gam[0]), Fr(gam[1]))
     xt = (G * (1 - t) + Cx(3 * t)) / (G * (1 - t) + Cx(2 * t))
     assert (cx_from(out["x_end"][0, :, :, 0]) - xt).absf() <= 8 * 2.0 ** (-53 * L)
+
+
+# ---- tangent predictor (Section 2's predictor stage, from J v = -dh/dt)
+def _diag_system(c):
+    n = len(c)
+    exps, coef = [], []
+    for i, ci in enumerate(c):
+        a = [0] * n
+        a[i] = 2
+        exps += [a, [0] * n]
+        coef += [[1.0, 0.0], [-ci.real, -ci.imag]]
+    return synth.System(n, n, np.full(n, 2, np.int32), np.array(exps, np.int8), np.array(coef))
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_tangent_of_the_diagonal_system_in_closed_form(oracle_lib, L):
+    """h_i = gamma (1 - t)(x_i^2 - 1) + t (x_i^2 - c_i): J = diag(2 x_i (gamma
+    (1 - t) + t)) and dh_i/dt = (x_i^2 - c_i) - gamma (x_i^2 - 1), so the
+    tangent at ANY point is v_i = -dh_i/dt / J_ii -- computed exactly with
+    rationals from the same doubles."""
+    from exact import Cx
+    from fractions import Fraction as F
+    c = np.array([0.3 + 0.8j, -1.1 + 0.2j, 0.5 - 0.9j])
+    s = _diag_system(c)
+    gam = (0.6, 0.8)
+    rng = synth.SplitMix64(17 + L)
+    for t in (0.0, 0.25, 0.625, 1.0):
+        x = synth.unit_points(40 + L, 3, 4, L)
+        x[:, :, 0, :] *= 0.5 + rng.uniform(12).reshape(3, 1, 4)  # off the path, |x| in (0.5, 1.5)
+        x[:, :, 1:, :] = 0.0
+        v = oracle_lib.tangent(s, [2, 2, 2], gam, t, x)
+        G = Cx(F(gam[0]), F(gam[1]))
+        T = F(t)
+        for p in range(4):
+            for i in range(3):
+                xi = Cx(F(x[i, 0, 0, p]), F(x[i, 1, 0, p]))
+                x2 = xi * xi
+                ht = (x2 - Cx(F(c[i].real), F(c[i].imag))) - G * (x2 - Cx(1))
+                Jii = Cx(2) * xi * (G * Cx(1 - T) + Cx(T))
+                want = Cx(0) - ht / Jii
+                got_re = sum(F(float(u)) for u in v[i, 0, :, p])
+                got_im = sum(F(float(u)) for u in v[i, 1, :, p])
+                err = float(abs(got_re - want.re) + abs(got_im - want.im))
+                assert err <= 2.0 ** (-53 * L + 10) * max(1.0, want.absf()), (t, p, i, err)
+
+
+def test_tangent_is_the_derivative_of_the_path(oracle_lib):
+    """On the diagonal system's path x_i(t)^2 = (gamma (1 - t) + t c_i) /
+    (gamma (1 - t) + t), the tangent equals the path's derivative (central
+    differences of the closed form)."""
+    c = np.array([0.3 + 0.8j, -1.1 + 0.2j, 0.5 - 0.9j])
+    s = _diag_system(c)
+    g = 0.6 + 0.8j
+    xt = lambda t: np.sqrt((g * (1 - t) + t * c) / (g * (1 - t) + t))
+    for t in (0.1, 0.5, 0.9):
+        z = xt(t)
+        x = np.zeros((3, 2, 1, 1))
+        x[:, 0, 0, 0], x[:, 1, 0, 0] = z.real, z.imag
+        v = oracle_lib.tangent(s, [2, 2, 2], (0.6, 0.8), t, x)
+        vz = v[:, 0, 0, 0] + 1j * v[:, 1, 0, 0]
+        h = 1e-5
+        fd = (xt(t + h) - xt(t - h)) / (2 * h)
+        assert np.max(np.abs(vz - fd)) <= 1e-8 * max(1.0, np.max(np.abs(fd))), (t, vz, fd)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_tangent_predictors_are_exact_on_polynomial_paths(oracle_lib, L):
+    """Euler reproduces paths linear in t, the cubic Hermite predictor paths
+    cubic in t, from exact dyadic data (values and derivatives)."""
+    from fractions import Fraction as F
+    from exact import fr
+    rng = synth.SplitMix64(700 + L)
+    n = 3
+    s0, s1, t1 = F(1, 8), F(3, 8), F(9, 16)
+    for mode, deg in ((1, 1), (2, 3)):
+        coef = rng.integers(-6, 6, 2 * n * (deg + 1)).reshape(n, 2, deg + 1)
+        p = lambda i, c, t: sum(F(int(coef[i, c, e])) * t ** e for e in range(deg + 1))
+        dp = lambda i, c, t: sum(e * F(int(coef[i, c, e])) * t ** (e - 1) for e in range(1, deg + 1))
+        arr = lambda f, t: np.array([[[float(f(i, c, t))] + [0.0] * (L - 1) for c in range(2)] for i in range(n)])
+        out = oracle_lib.predict_tangent(mode, float(s0), arr(p, s0), arr(dp, s0), float(s1), arr(p, s1),
+                                         arr(dp, s1), float(t1))
+        for i in range(n):
+            for c in range(2):
+                err = abs(fr(out[i, c]) - p(i, c, t1))
+                assert err <= 2.0 ** (-53 * L + 12) * 64, (mode, i, c, float(err))
+        # at s1 the predictor returns x1; a path one degree higher is missed
+        # by exactly its top coefficient times the predictor's known error
+        # factor (Euler: (t1 - s1)^2; Hermite: (t1 - s0)^2 (t1 - s1)^2)
+        out_s1 = oracle_lib.predict_tangent(mode, float(s0), arr(p, s0), arr(dp, s0), float(s1), arr(p, s1),
+                                            arr(dp, s1), float(s1))
+        assert np.array_equal(out_s1[:, :, 0], arr(p, s1)[:, :, 0])
+        q = lambda i, c, t: p(i, c, t) + t ** (deg + 1)
+        dq = lambda i, c, t: dp(i, c, t) + (deg + 1) * t ** deg
+        out_q = oracle_lib.predict_tangent(mode, float(s0), arr(q, s0), arr(dq, s0), float(s1), arr(q, s1),
+                                           arr(dq, s1), float(t1))
+        miss = (t1 - s1) ** 2 if mode == 1 else (t1 - s0) ** 2 * (t1 - s1) ** 2
+        for i in range(n):
+            err = fr(out_q[i, 0]) - q(i, 0, t1)
+            assert abs(err + miss) <= 2.0 ** (-53 * L + 12) * 64, (mode, float(err), float(miss))
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("pred", [1, 2])
+def test_tangent_predictors_track_the_diagonal_system(oracle_lib, L, pred):
+    """Every path of x_i^2 = c_i ends at its closed-form root with either
+    tangent predictor, in D, DD and QD."""
+    c = np.array([0.3 + 0.8j, -1.1 + 0.2j, 0.5 - 0.9j])
+    s = _diag_system(c)
+    o = oracle_lib.track(s, [2, 2, 2], (0.6, 0.8), np.arange(8), L, oracle_lib.default_params(L, predictor=pred))
+    assert np.all(o["status"] == 1)
+    r = np.sqrt(c)
+    z = (o["x_end"][:, 0, 0, :] + 1j * o["x_end"][:, 1, 0, :]).T
+    for p in range(8):
+        want = [r[i] * (1 - 2 * ((p >> i) & 1)) for i in range(3)]
+        assert np.max(np.abs(z[p] - want)) <= 1e-13, (p, z[p], want)
+
+
+def test_hermite_takes_fewer_steps_than_euler(oracle_lib):
+    """Both tangent predictors reach the same endpoints of the n = 6 system;
+    the third-order Hermite predictor needs fewer steps than first-order
+    Euler."""
+    s = synth.config_system("plain_n6_d")
+    g = synth.random_gamma(0)
+    res = {}
+    for pred in (1, 2):
+        res[pred] = oracle_lib.track(s, s.degrees(), g, np.arange(16), 1,
+                                     oracle_lib.default_params(1, h_min=1e-6, predictor=pred))
+    assert np.all(res[1]["status"] == 1) and np.all(res[2]["status"] == 1)
+    za = (res[1]["x_end"][:, 0, 0, :] + 1j * res[1]["x_end"][:, 1, 0, :]).T
+    zb = (res[2]["x_end"][:, 0, 0, :] + 1j * res[2]["x_end"][:, 1, 0, :]).T
+    assert np.max(np.abs(za - zb)) <= 1e-10
+    assert res[2]["steps"].sum() < res[1]["steps"].sum()
