@@ -101,6 +101,8 @@ def _args():
                    help="paths of the held-out n = 10 quad double system for learned vs plain (0: skip)")
     p.add_argument("--no-ablation", action="store_true",
                    help="skip the three-kernel (coeff, mon, sum) evaluation against the fused kernel")
+    p.add_argument("--no-predictors", action="store_true",
+                   help="skip the comparison of the extrapolation, Euler and Hermite predictors")
     p.add_argument("--no-quality-up", action="store_true",
                    help="skip the mixed-precision (double tracking, double double refinement) comparison")
     p.add_argument("--no-paper-sweep", action="store_true",
@@ -299,6 +301,42 @@ def unfused_ablation(ht, torch, stream, flush, system, xs, n, fused_ms):
             "unfused_over_fused": tot / fused_ms[L]}
         del val, jac
     return out
+
+
+def predictor_comparison(ht, torch, world, name="batched_n12_dd", h_min=1e-6):
+    """The three predictors of the tracker on one workload (Section 2's
+    predictor stage): extrapolation through up to five accepted points (0),
+    Euler (1) and cubic Hermite (2) on the path's tangent from J v = -dh/dt.
+    Per predictor: wall time, steps and Newton rounds per path, status
+    counts, and the endpoints' agreement with the extrapolation run."""
+    L = TRACK_LIMBS[name]
+    s = synth.config_system(name)
+    gam = synth.random_gamma(synth.CONFIGS[name]["seed"])
+    m = int(np.prod(s.degrees().astype(np.int64)))
+    hs = ht.system_from(s, L)
+    out, ends = {}, {}
+    for pred in (0, 1, 2):
+        prm = ht.ht_default_params(L, h_min=h_min, predictor=pred)
+        x = torch.empty((s.n_vars, 2, L, m), dtype=torch.float64, device="cuda")
+        st = torch.empty((m,), dtype=torch.int8, device="cuda")
+        t = torch.empty((m,), dtype=torch.float64, device="cuda")
+        stats = ht.ht_stats()
+        ht.ht_track_paths(hs, s.degrees(), gam, m, 0, None, prm, x, st, t, None, stats)  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ht.ht_track_paths(hs, s.degrees(), gam, m, 0, None, prm, x, st, t, None, stats)
+        torch.cuda.synchronize()
+        sec = time.perf_counter() - t0
+        d = stats.as_dict()
+        xs = x.cpu().numpy()
+        ok = st.cpu().numpy() == 1
+        ends[pred] = (xs[:, 0, 0, :] + 1j * xs[:, 1, 0, :]).T[ok]
+        out[{0: "extrapolation", 1: "euler", 2: "hermite"}[pred]] = {
+            "s": sec, "paths_per_s": world * m / sec, "steps_per_path": d["steps"] / m,
+            "newton_per_path": d["newton"] / m, "rejects_per_path": d["rejects"] / m,
+            "counts": {k: d[k] for k in ("converged", "failed", "diverged")},
+            "endpoint_agreement_with_extrapolation_1e-10": _agreement(ends[0], ends[pred]) if pred else 1.0}
+    return {"workload": name, "paths": m, "precision": NAMES[L], "h_min": h_min, "by_predictor": out}
 
 
 def quality_up(ht, torch, world, name="batched_n12_dd", Lh=2, h_min=1e-6):
@@ -687,6 +725,8 @@ def run_ours(a):
                                                                ORACLE_TRACK_SAMPLE[name])
     if not a.no_quality_up:
         tracking["quality_up_n12_dd"] = quality_up(ht, torch, world)
+    if not a.no_predictors:
+        tracking["predictors_n12_dd"] = predictor_comparison(ht, torch, world)
     for name, m, key in (("learned_n16_d", a.learned, "learned_n16_d_vs_plain"),
                          ("stress_n10_qd", a.stress, "stress_n10_qd_vs_plain")):
         if m > 0:

@@ -252,6 +252,13 @@ typedef struct ht_params {
   int32_t team_warps;       /* warps serving one group of 32 paths (1..8); 0 = chosen per round */
   int32_t iters_per_launch; /* Newton steps per kernel launch; 0 = default (4) */
   int32_t rounds_per_sync;  /* launches between host reads of the active count, even; 0 = default (8) */
+  int32_t predictor;        /* 0 extrapolation through up to max_order + 1 accepted points (default);
+                               1 Euler and 2 cubic Hermite on the path's tangent v = dx/dt, which each
+                               Newton round also solves from J v = -dh/dt with the same factorisation
+                               (Euler: x + (t1 - t) v at the current point; Hermite: the cubic matching
+                               the current and the previous accepted point and their tangents).  The
+                               start point has no tangent: until one exists the step predicts x itself,
+                               and Hermite uses Euler while only the current point has one */
 } ht_params;
 
 /* Counts of one ht_track_paths call. */
@@ -265,7 +272,7 @@ typedef struct ht_stats {
 
 /* Defaults for `limbs` (HT_D, HT_DD, HT_QD): h0 0.05, h_min 1e-5, h_max 0.1,
  * f_up 1.5, f_down 0.5, tol_dx 1e-6, tol_res 1e-4, tol_polish 1e-12 / 1e-24 /
- * 1e-48, r_div 1e8, newton_max 3, polish_max 4, max_steps 2000, max_order 4. */
+ * 1e-48, r_div 1e8, newton_max 3, polish_max 4, max_steps 2000, max_order 4, predictor 0. */
 int ht_default_params(int limbs, ht_params* p);
 
 /*

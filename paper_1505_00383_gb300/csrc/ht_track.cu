@@ -232,6 +232,7 @@ __global__ void init_kernel(TrackArgs a) {
     a.it[p] = 0;
     a.phase[p] = (a.polish_only && !a.init_rec) ? PH_POLISH : PH_TRACK;
     a.fallback[p] = 0;
+    a.ntan[p] = 0;
     a.steps[p] = 0;
     a.rejects[p] = 0;
     a.newton[p] = 0;
@@ -287,8 +288,8 @@ __device__ __forceinline__ rl<L> acc_abs2(rl<L> s, const cx<L>& v) {
 
 template <int L>
 __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
-                         int warp, int T) {
-  const int W = cols + 1;
+                         int warp, int T, int nrhs = 1, double* x2 = nullptr) {
+  const int W = cols + nrhs;
   rl<L> nrm_next = r_from<L>(0.0);
   if (warp == 0 && act) {
     rl<L> s = r_from<L>(0.0);
@@ -309,7 +310,7 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
     }
     __syncthreads();
     int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
-    for (int j = j0; j <= cols; j += T) {
+    for (int j = j0; j < W; j += T) {
       if (!act) continue;
       cx<L> r = czero<L>();
       for (int i = 0; i < rows; ++i)
@@ -326,11 +327,14 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
     }
     __syncthreads();
   }
-  if (warp == 0 && act) {
+  // back substitution, the right-hand sides dealt to the warps (the second
+  // solves into x2)
+  for (int k = warp; act && k < nrhs; k += T) {
+    double* xs = k == 0 ? x : x2;
     for (int q = cols - 1; q >= 0; --q) {
-      cx<L> acc = ld<L>(R, (int64_t)q * W + cols, m, p);
-      for (int j = q + 1; j < cols; ++j) acc = sub_mul<L>(acc, ld<L>(R, (int64_t)q * W + j, m, p), ld<L>(x, j, m, p));
-      st<L>(x, q, m, p, cscale_r(acc, ld<L>(R, (int64_t)q * W + q, m, p).re));
+      cx<L> acc = ld<L>(R, (int64_t)q * W + cols + k, m, p);
+      for (int j = q + 1; j < cols; ++j) acc = sub_mul<L>(acc, ld<L>(R, (int64_t)q * W + j, m, p), ld<L>(xs, j, m, p));
+      st<L>(xs, q, m, p, cscale_r(acc, ld<L>(R, (int64_t)q * W + q, m, p).re));
     }
   }
   __syncthreads();
@@ -367,10 +371,10 @@ __device__ __forceinline__ void stz(double* base, int64_t e, int64_t m, int64_t 
 
 template <int L, int N>
 __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
-                             int warp, int T) {
+                             int warp, int T, int nrhs = 1, double* x2 = nullptr) {
   constexpr int W = IntW<L>::W;  // rows <= N
   using Z = mpi::fz<W>;
-  const int Wc = cols + 1;
+  const int Wc = cols + nrhs;
   Z Q[N], col[N], S[N + 1];
   for (int q = 0; q < cols; ++q) {
     if (warp == q % T && act) {
@@ -382,9 +386,9 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
     }
     __syncthreads();
     const int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
-    if (act && j0 <= cols) {
+    if (act && j0 < Wc) {
       for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc + q, m, p);
-      for (int j = j0; j <= cols; j += T) {
+      for (int j = j0; j < Wc; j += T) {
         for (int i = 0; i < rows; ++i) col[i] = ldz<L>(A, (int64_t)i * Wc + j, m, p);
         const Z r = mpi::dot_conj<W, N>(Q, col, rows, S);
         stz<L>(R, (int64_t)q * Wc + j, m, p, r);
@@ -394,14 +398,16 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
     }
     __syncthreads();
   }
-  if (warp == 0 && act) {  // back substitution, solution in col[]
+  // back substitution, the right-hand sides dealt to the warps, solution in col[]
+  for (int r = warp; act && r < nrhs; r += T) {
     for (int q = cols - 1; q >= 0; --q) {
       int k = 0;
-      S[k++] = ldz<L>(R, (int64_t)q * Wc + cols, m, p);
+      S[k++] = ldz<L>(R, (int64_t)q * Wc + cols + r, m, p);
       for (int j = q + 1; j < cols; ++j) S[k++] = mpi::mul<W>(ldz<L>(R, (int64_t)q * Wc + j, m, p), col[j]);
       col[q] = mpi::mul<W>(mpi::first_minus_rest<W, N + 1>(S, k), ldz<L>(R, (int64_t)q * Wc + q, m, p));
     }
-    for (int q = 0; q < cols; ++q) stz<L>(x, q, m, p, col[q]);
+    double* xs = r == 0 ? x : x2;
+    for (int q = 0; q < cols; ++q) stz<L>(xs, q, m, p, col[q]);
   }
   __syncthreads();
 }
@@ -478,7 +484,9 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
   float* lgs_int = reinterpret_cast<float*>(xs_int + (int64_t)a.n * (2 * IntW<L>::W + 1) * 32);
   const int cap = a.prm.max_order + 1;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, T = blockDim.x >> 5;
-  const int n = a.n, W = n + 1;
+  // the tangent predictors solve J v = -dh/dt as a second right-hand side
+  const int pmode = a.prm.predictor, nrhs = pmode > 0 ? 2 : 1;
+  const int n = a.n, W = n + nrhs;
   const int64_t m = a.m;
   const int count = *a.count_in;
   const int64_t rowA = (int64_t)W * 2 * L * m;  // doubles per row of A
@@ -504,6 +512,7 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
       int it = act ? a.it[p] : 0;
       double t = act ? a.t[p] : 0.0, h = act ? a.h[p] : 0.0, t1 = act ? a.t1[p] : 0.0;
       int nh = act ? a.nh[p] : 1;
+      int ntan = act && pmode > 0 ? a.ntan[p] : 0;
       int fb = act ? a.fallback[p] : 0;
       double alpha = 0.0;  // tangent correction of a learned step (0: the plain predictor)
       const bool start = act && ph == PH_TRACK && it == 0;
@@ -557,8 +566,24 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
       if (start) {
         double step = fmin(h, 1.0 - t);
         t1 = (step >= 1.0 - t) ? 1.0 : t + step;
-        const int mm = min(nh, a.prm.max_order + 1);
+        // tangent predictors: cubic Hermite on the last two points and their
+        // tangents, Euler on the last one; until a tangent exists, x itself
+        const bool herm = pmode == 2 && ntan >= 2 && nh >= 2, euler = !herm && pmode >= 1 && ntan >= 1;
+        const int mm = (herm || euler) ? 0 : (pmode >= 1 ? 1 : min(nh, a.prm.max_order + 1));
         const int base = nh - mm;
+        rl<L> ca = r_from<L>(0.0), cb = r_from<L>(0.0), cc = r_from<L>(0.0), cd = r_from<L>(0.0);
+        if (herm) {  // x0, v0 at s0 = ht[nh-2]; x1, v1 at s1 = ht[nh-1]
+          const double s0 = a.ht[(int64_t)(nh - 2) * m + p], s1 = a.ht[(int64_t)(nh - 1) * m + p];
+          const rl<L> d = r_diff<L>(s1, s0), u = r_div(r_diff<L>(t1, s0), d);
+          const rl<L> u2 = r_mul(u, u), u3 = r_mul(u2, u);
+          const rl<L> two = r_from<L>(2.0), three = r_from<L>(3.0);
+          ca = r_add(r_sub(r_mul(two, u3), r_mul(three, u2)), r_from<L>(1.0));  // weight of x0
+          cb = r_mul(r_add(r_sub(u3, r_mul(two, u2)), u), d);                  // of v0
+          cc = r_sub(r_mul(three, u2), r_mul(two, u3));                        // of x1
+          cd = r_mul(r_sub(u3, u2), d);                                        // of v1
+        } else if (euler) {
+          cd = r_diff<L>(t1, a.ht[(int64_t)(nh - 1) * m + p]);
+        }
         rl<L> w[8];
         for (int j = 0; j < mm; ++j) {
           rl<L> num = r_from<L>(1.0), den = r_from<L>(1.0);
@@ -575,6 +600,15 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
           cx<L> acc = czero<L>();
           for (int j = 0; j < mm; ++j)
             acc = cadd(acc, cscale_r(ld<L>(a.hx, (int64_t)(base + j) * n + i, m, p), w[j]));
+          if (herm) {
+            acc = cscale_r(ld<L>(a.hx, (int64_t)(nh - 2) * n + i, m, p), ca);
+            acc = cadd(acc, cscale_r(ld<L>(a.tx, (int64_t)(nh - 2) * n + i, m, p), cb));
+            acc = cadd(acc, cscale_r(ld<L>(a.hx, (int64_t)(nh - 1) * n + i, m, p), cc));
+            acc = cadd(acc, cscale_r(ld<L>(a.tx, (int64_t)(nh - 1) * n + i, m, p), cd));
+          } else if (euler) {
+            acc = cadd(ld<L>(a.hx, (int64_t)(nh - 1) * n + i, m, p),
+                       cscale_r(ld<L>(a.tx, (int64_t)(nh - 1) * n + i, m, p), cd));
+          }
           if (alpha != 0.0) {  // learned tangent correction: x + (1 + alpha)(pred - x)
             const cx<L> xc = ld<L>(a.hx, (int64_t)(nh - 1) * n + i, m, p);
             acc = cadd(xc, cscale_r(csub(acc, xc), r_from<L>(1.0 + alpha)));
@@ -633,6 +667,7 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
           cx<L> mh = czero<L>();
           mh = csub(mh, hj);
           st<L>(Arow, n, m, p, mh);
+          if (nrhs == 2) st<L>(Arow, n + 1, m, p, csub(cmul(gamma, gval), fj));  // -dh/dt = gamma g - f
           pres = nanmax(pres, cfinite(hj) ? cabs_lead(hj) : __longlong_as_double(0x7ff8000000000000LL));
         }
       }
@@ -642,9 +677,9 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
       // instructions, and there the FP64 MGS was measured faster (1.6 s
       // against 3.1 s for the whole n = 12, 4,096-path DD run)
       if constexpr (INT && L == 4)
-        mgs_team_int<L, kIntMaxTrack>(a.A, a.R, a.dx, n, n, m, p, act, warp, T);
+        mgs_team_int<L, kIntMaxTrack>(a.A, a.R, a.dx, n, n, m, p, act, warp, T, nrhs, a.tdx);
       else
-        mgs_team<L>(a.A, a.R, a.dx, n, n, m, p, act, warp, T);
+        mgs_team<L>(a.A, a.R, a.dx, n, n, m, p, act, warp, T, nrhs, a.tdx);
       // ---- D: x <- x + dx on this warp's coordinates; partial norms
       double pdx = 0.0, pxp = 0.0;
       if (act) {
@@ -741,6 +776,16 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
               for (int s = 0; s + 1 < cap; ++s) st<L>(a.hx, (int64_t)s * n + i, m, p, ld<L>(a.hx, (int64_t)(s + 1) * n + i, m, p));
               st<L>(a.hx, (int64_t)(cap - 1) * n + i, m, p, xv);
             }
+            if (pmode > 0) {  // the tangent of the accepted point: its last round's second solution
+              const cx<L> tv = ld<L>(a.tdx, i, m, p);
+              if (nh < cap) {
+                st<L>(a.tx, (int64_t)nh * n + i, m, p, tv);
+              } else {
+                for (int s = 0; s + 1 < cap; ++s)
+                  st<L>(a.tx, (int64_t)s * n + i, m, p, ld<L>(a.tx, (int64_t)(s + 1) * n + i, m, p));
+                st<L>(a.tx, (int64_t)(cap - 1) * n + i, m, p, tv);
+              }
+            }
           }
         }
       }
@@ -762,6 +807,7 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
         }
         if (push_hist) {
           const int cap = a.prm.max_order + 1;
+          if (pmode > 0) a.ntan[p] = (int8_t)min(ntan + 1, cap);
           if (nh < cap) {
             a.ht[(int64_t)nh * m + p] = t;
             ++nh;

@@ -22,6 +22,7 @@ constexpr int FEAT = 16;
 struct TrackPrm {
   double h0, h_min, h_max, f_up, f_down, tol_dx, tol_res, tol_polish, r_div;
   int newton_max, polish_max, max_steps, max_order, deg_max;
+  int predictor;  // 0 extrapolation, 1 Euler, 2 cubic Hermite on tangents
 };
 
 // Device pointers of the homotopy and of the per-path state, all paths' values
@@ -44,9 +45,12 @@ struct TrackArgs {
   double* xp;  // [n]     working point
   double* hx;  // [cap][n] accepted history, oldest first (cap = max_order + 1)
   double* ht;  // [cap]   their t values
-  double* A;   // [n][n+1] [J | -h], then Q
-  double* R;   // [n][n+1] triangular factor, 1/r_qq on the diagonal
+  double* A;   // [n][n+nrhs] [J | -h (| -dh/dt)], then Q
+  double* R;   // [n][n+nrhs] triangular factor, 1/r_qq on the diagonal
   double* dx;  // [n]
+  double* tx;  // [cap][n] tangents of the history points (predictor > 0)
+  double* tdx; // [n]     tangent solved in the latest Newton round
+  int8_t* ntan;  // history points, most recent first, that carry a tangent
   double* t;   // the caller's t_end
   double* h;
   double* t1;

@@ -265,7 +265,8 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   if (!(P.h0 > 0) || !(P.h_min > 0) || !(P.h_max >= P.h_min) || !(P.f_up >= 1) || !(P.f_down > 0 && P.f_down < 1) ||
       P.newton_max < 1 || P.newton_max > 100 || P.polish_max < 0 || P.polish_max > 100 || P.max_steps < 1 ||
       P.max_order < 0 || P.max_order > 7 || P.team_warps < 0 || P.team_warps > 8 || P.iters_per_launch < 0 ||
-      P.rounds_per_sync < 0 || (P.rounds_per_sync & 1) || !(P.tol_dx > 0) || !(P.tol_res > 0) || !(P.tol_polish > 0) || !(P.r_div > 0))
+      P.rounds_per_sync < 0 || (P.rounds_per_sync & 1) || !(P.tol_dx > 0) || !(P.tol_res > 0) || !(P.tol_polish > 0) || !(P.r_div > 0) ||
+      P.predictor < 0 || P.predictor > 2)
     return set_error(HT_EINVAL, "ht_track_paths: invalid parameters");
   ht_track_io IO;
   std::memset(&IO, 0, sizeof IO);
@@ -302,8 +303,11 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
     off += up256(b);
     return o;
   };
+  const int nrhs = P.predictor > 0 ? 2 : 1;  // the tangent predictors add J v = -dh/dt
   size_t o_xp = take(n * cxb), o_hx = take((size_t)cap * n * cxb), o_ht = take((size_t)cap * m * 8),
-         o_A = take((size_t)n * (n + 1) * cxb), o_R = take((size_t)n * (n + 1) * cxb), o_dx = take(n * cxb),
+         o_A = take((size_t)n * (n + nrhs) * cxb), o_R = take((size_t)n * (n + nrhs) * cxb), o_dx = take(n * cxb),
+         o_tx = P.predictor > 0 ? take((size_t)cap * n * cxb) : 0, o_tdx = P.predictor > 0 ? take(n * cxb) : 0,
+         o_ntan = take(m),
          o_h = take(m * 8), o_t1 = take(m * 8), o_it = take(m), o_ph = take(m), o_nh = take(m),
          o_steps = take(m * 4), o_rej = take(m * 4), o_newt = take(m * 4), o_idx0 = take((m + 1) * 4),
          o_idx1 = take((m + 1) * 4), o_cnt = take(2 * 4), o_deg = take(n * 4), o_ldx = take(m * 8),
@@ -329,7 +333,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.n = n;
   a.m = m;
   a.prm = TrackPrm{P.h0, P.h_min, P.h_max, P.f_up, P.f_down, P.tol_dx, P.tol_res, P.tol_polish, P.r_div,
-                   P.newton_max, P.polish_max, P.max_steps, P.max_order, deg_max};
+                   P.newton_max, P.polish_max, P.max_steps, P.max_order, deg_max, P.predictor};
   a.x = x_end;
   a.xp = (double*)(w + o_xp);
   a.hx = (double*)(w + o_hx);
@@ -337,6 +341,9 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.A = (double*)(w + o_A);
   a.R = (double*)(w + o_R);
   a.dx = (double*)(w + o_dx);
+  a.tx = P.predictor > 0 ? (double*)(w + o_tx) : nullptr;
+  a.tdx = P.predictor > 0 ? (double*)(w + o_tdx) : nullptr;
+  a.ntan = (int8_t*)(w + o_ntan);
   a.t = t_end;
   a.h = (double*)(w + o_h);
   a.t1 = (double*)(w + o_t1);

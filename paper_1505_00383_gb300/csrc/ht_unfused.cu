@@ -33,7 +33,8 @@ __global__ void uf_coeff_kernel(const double* __restrict__ coef, int64_t M, int6
   }
 }
 
-// mon: block (points, monomial m = blockIdx.y).  Row slot_off[m] of mon gets
+// mon: block (points, monomial m = blockIdx.y).  Row slot_off[m] of the
+// workspace (rows counted from its start, past the M coefficient rows) gets
 // the value, rows slot_off[m] + 1 + r the derivative by the r-th variable of
 // the support (without the exponent factor).
 template <int L>
@@ -112,8 +113,10 @@ int launch_unfused_l(const ht_system* s, int64_t n, int64_t p0, int64_t cc, cons
   const int32_t* out_slot = out_off + n_out + 1;
   const int32_t* out_exp = out_slot + s->uf_terms;
   const int32_t* slot_off = out_exp + s->uf_terms;
-  double* cff = ws;                                   // rows 0 .. M-1
-  double* mon = ws + (int64_t)s->M * 2 * L * cc;      // rows of slot_off
+  // one array of rows: the coefficients in rows 0 .. M-1, the monomials'
+  // values and derivatives in the rows slot_off[m] .. (slot_off[0] = M)
+  double* cff = ws;
+  double* mon = ws;
   const unsigned gx = (unsigned)((cc + 127) / 128);
   if (ev) cudaEventRecord(ev[0], st);
   int64_t blocks = (s->M * cc + 255) / 256;

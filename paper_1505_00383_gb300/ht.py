@@ -67,7 +67,7 @@ class ht_params(ctypes.Structure):
     _fields_ = [(k, ctypes.c_double) for k in ("h0", "h_min", "h_max", "f_up", "f_down", "tol_dx", "tol_res",
                                                 "tol_polish", "r_div")] + \
                [(k, ctypes.c_int32) for k in ("newton_max", "polish_max", "max_steps", "max_order", "team_warps",
-                                               "iters_per_launch", "rounds_per_sync")]
+                                               "iters_per_launch", "rounds_per_sync", "predictor")]
 
 
 class ht_track_io(ctypes.Structure):

@@ -326,8 +326,9 @@ def test_unfused_three_kernels_equal_the_fused_kernel(ht, name, L):
 
 
 def test_unfused_in_chunks_at_full_size(ht):
-    """65,536 points in QD need several workspace chunks: sampled points of
-    the last chunks against the fused kernel, bit for bit."""
+    """65,536 points in QD need 29 workspace chunks of 2,304 points: points
+    at chunk edges and in the last chunk against the fused kernel, bit for
+    bit."""
     s = synth.config_system("evaldiff_n32")
     n, L = 65536, 4
     x = torch.from_numpy(synth.unit_points(1004, s.n_vars, n, L)).cuda()
@@ -339,6 +340,6 @@ def test_unfused_in_chunks_at_full_size(ht):
         jac = torch.full((s.n_polys, s.n_vars, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
         (ht.ht_eval_diff_unfused if unfused else ht.ht_eval_diff)(hs, n, x, val, jac)
         torch.cuda.synchronize()
-        pts = torch.tensor([0, 2047, 2048, 40000, n - 1], device="cuda")
+        pts = torch.tensor([0, 2303, 2304, 40000, 64511, 64512, n - 1], device="cuda")
         res.append((val[..., pts].cpu().numpy(), jac[..., pts].cpu().numpy()))
     assert np.array_equal(res[0][0], res[1][0]) and np.array_equal(res[0][1], res[1][1])

@@ -510,3 +510,70 @@ def test_full_workload_matches_oracle_on_1024_sampled_paths(ht, name):
     err = np.max(np.maximum(np.abs(zg.real - zo.real), np.abs(zg.imag - zo.imag)), axis=1) / scale
     assert np.all(err <= 1e-10), (np.max(err), ids[conv][np.argmax(err)])
     assert np.all(t.cpu().numpy()[ids][conv] == 1.0)
+
+
+# ---- tangent predictors (Euler, cubic Hermite on J v = -dh/dt)
+@pytest.mark.parametrize("pred", [1, 2])
+def test_tangent_predictors_n6_match_oracle_path_by_path(ht, pred):
+    """64 paths of the n = 6 system with the Euler (1) and Hermite (2)
+    predictors: the same status, number of steps and endpoint as the oracle's
+    tracker with the same predictor, path by path."""
+    s = synth.config_system("plain_n6_d")
+    gam = synth.random_gamma(0)
+    g = track_gpu(ht, s, 1, 64, gamma=gam, h_min=1e-6, predictor=pred)
+    o = track_oracle(s, 1, np.arange(64), gamma=gam, h_min=1e-6, predictor=pred)
+    assert_same_outcome(g, o)
+    assert np.array_equal(g["status"], o["status"])
+    assert np.array_equal(g["steps"], o["steps"])
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+@pytest.mark.parametrize("pred", [1, 2])
+def test_tangent_predictors_diagonal_closed_form(ht, L, pred):
+    c = np.array([0.3 + 0.8j, -1.1 + 0.2j, 0.5 - 0.9j])
+    exps, coef = [], []
+    for i, ci in enumerate(c):
+        a = [0, 0, 0]
+        a[i] = 2
+        exps += [a, [0, 0, 0]]
+        coef += [[1.0, 0.0], [-ci.real, -ci.imag]]
+    s = synth.System(3, 3, np.full(3, 2, np.int32), np.array(exps, np.int8), np.array(coef))
+    g = track_gpu(ht, s, L, 8, predictor=pred)
+    assert np.all(g["status"] == 1)
+    o = track_oracle(s, L, np.arange(8), predictor=pred)
+    assert_same_outcome(g, o)
+    e = cerr(g["x_end"], o["x_end"])
+    assert np.max(e) <= {1: 1e-13, 2: 1e-26, 4: 1e-50}[L]
+
+
+@pytest.mark.parametrize("name,L,m,sample", [("batched_n12_dd", 2, 4096, 16), ("stress_n10_qd", 4, 512, 4)])
+def test_hermite_predictor_batched_sampled_paths_match_oracle(ht, name, L, m, sample):
+    """The Hermite predictor on the workload shapes (integer-pipe evaluation;
+    QD also solves both right-hand sides on the integer pipe): a seeded
+    sample of paths tracked by the oracle ends with the same status and
+    endpoint."""
+    s = synth.config_system(name)
+    gam = synth.random_gamma(synth.CONFIGS[name]["seed"])
+    g = track_gpu(ht, s, L, m, gamma=gam, h_min=1e-6, predictor=2)
+    rng = synth.SplitMix64(8)
+    ids = np.unique(np.concatenate([[0, m - 1], rng.integers(0, m - 1, sample)]))
+    o = track_oracle(s, L, ids, gamma=gam, h_min=1e-6, predictor=2)
+    assert np.array_equal(g["status"][ids], o["status"])
+    conv = o["status"] == 1
+    e = cerr(g["x_end"][..., ids][..., conv], o["x_end"][..., conv])
+    scale = np.maximum(1.0, np.max(np.abs(to_complex(o["x_end"][..., conv])), axis=1))
+    assert np.all(np.max(e, axis=0) / scale <= 1e-10)
+
+
+@pytest.mark.parametrize("L", [1, 4])
+def test_hermite_results_do_not_depend_on_the_launch_shape(ht, L):
+    """Both right-hand sides are dealt to the team's warps; any team size
+    gives the same bits."""
+    s = synth.config_system("stress_n10_qd" if L == 4 else "plain_n6_d")
+    gam = synth.random_gamma(1)
+    base = track_gpu(ht, s, L, 96 if L == 4 else 64, gamma=gam, team_warps=1, iters_per_launch=2,
+                     rounds_per_sync=2, predictor=2)
+    for tw in (2, 8):
+        r = track_gpu(ht, s, L, 96 if L == 4 else 64, gamma=gam, team_warps=tw, predictor=2)
+        for k in ("x_end", "status", "t_end", "steps"):
+            assert np.array_equal(r[k], base[k], equal_nan=True), (tw, k)
