@@ -69,7 +69,7 @@ def eval_ops_per_point(system, L):
 # products (Gauss's form), each over the limb pairs whose column is kept
 # (x + y >= W - 2).
 INT_W = {1: 3, 2: 5, 4: 8}
-VARIANT_NAMES = {0: "unrolled fp64", 1: "compact fp64", 2: "integer limbs"}
+VARIANT_NAMES = {0: "unrolled fp64", 1: "compact fp64", 2: "integer limbs", 3: "three kernels fp64"}
 
 
 def int_products_per_point(system, L):
@@ -500,9 +500,10 @@ PAPER_GPU_MS = {
 
 def paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak, reps=10):
     """ht_eval_diff on the stand-ins shaped like the paper's applications at
-    the point counts of its evaluation tables: per shape and precision the
-    autotuner's choice at 3,000 points, then the median of `reps` launches per
-    point count (CUDA events, L2 flushed before each)."""
+    the point counts of its evaluation tables: per shape, precision and point
+    count the autotuner's choice (fused FP64 bodies, integer limbs, or the
+    three kernels, which spread few points' work over monomials), then the
+    median of `reps` launches (CUDA events, L2 flushed before each)."""
     out = {}
     for name in ("cyclic10_shape", "nash8_shape", "pieri44_shape"):
         system = synth.config_system(name)
@@ -513,13 +514,12 @@ def paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak, reps=10):
             x = torch.from_numpy(synth.unit_points(900 + L, system.n_vars, nmax, L)).cuda()
             val = torch.empty((system.n_polys, 2, L, nmax), dtype=torch.float64, device="cuda")
             jac = torch.empty((system.n_polys, system.n_vars, 2, L, nmax), dtype=torch.float64, device="cuda")
-            v, t, _ = ht.ht_tune_eval(hs, nmax, x, val, jac, reps=3)
             rows = {}
             for n in synth.PAPER_SWEEP_POINTS:
                 xs = x[..., :n].contiguous()
                 vs = torch.empty((system.n_polys, 2, L, n), dtype=torch.float64, device="cuda")
                 js = torch.empty((system.n_polys, system.n_vars, 2, L, n), dtype=torch.float64, device="cuda")
-                ht.ht_eval_diff(hs, n, xs, vs, js, stream)
+                v, t, _ = ht.ht_tune_eval(hs, n, xs, vs, js, reps=3)  # the autotuner's choice at this size
                 ms = []
                 for _ in range(reps):
                     flush.zero_()
@@ -530,8 +530,8 @@ def paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak, reps=10):
                     torch.cuda.synchronize()
                     ms.append(e0.elapsed_time(e1))
                 m = statistics.median(ms)
-                row = {"ms": m, "pts_per_s": n / (m * 1e-3)}
-                if v >= 2:
+                row = {"ms": m, "pts_per_s": n / (m * 1e-3), "variant": VARIANT_NAMES[v], "threads": t}
+                if v == 2:
                     row["imad_frac"] = int_products_per_point(system, L) * n / (m * 1e-3) / imad_peak
                 else:
                     row["fp64_frac"] = eval_ops_per_point(system, L) * n / (m * 1e-3) / fp64_peak
@@ -539,7 +539,7 @@ def paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak, reps=10):
                 if paper is not None:
                     row["paper_k20c_ms"] = paper
                 rows[n] = row
-            res[NAMES[L]] = {"variant": VARIANT_NAMES[v], "threads": t, "by_points": rows}
+            res[NAMES[L]] = {"by_points": rows}
         out[name] = res
     return out
 
@@ -605,7 +605,7 @@ def run_ours(a):
     # (FP64-pipe utilisation of the error-free DD/QD arithmetic)
     fp64_ref = {}
     for L in PRECISIONS:
-        if variant[L] >= 2:
+        if variant[L] == 2:
             ht.ht_set_eval_config(sys_h[L], 1, 256)
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             flush.zero_()
@@ -670,7 +670,7 @@ def run_ours(a):
     dom = max(PRECISIONS, key=lambda L: statistics.mean(launch_ms[L]))
     dom_ms = statistics.mean(launch_ms[dom])
     tr = _traffic(dom)
-    if variant[dom] >= 2:
+    if variant[dom] == 2:
         work = int_products_per_point(system, dom) * n
         achieved = work / (dom_ms * 1e-3)
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": imad_peak / 1e12,
@@ -693,7 +693,7 @@ def run_ours(a):
         m = statistics.mean(launch_ms[L])
         d = {"ms": m, "pts_per_s": n / (m * 1e-3), "variant": tuned[NAMES[L]]["variant"],
              "out_GB_per_s": (system.n_polys * (system.n_vars + 1) * 16 * L * n) / (m * 1e-3) / 1e9}
-        if variant[L] >= 2:
+        if variant[L] == 2:
             d["imad_frac"] = int_products_per_point(system, L) * n / (m * 1e-3) / imad_peak
             if L in fp64_ref:
                 d["fp64_bodies"] = {"ms": fp64_ref[L], "pts_per_s": n / (fp64_ref[L] * 1e-3),

@@ -100,12 +100,14 @@ int ht_eval_diff(const ht_system* sys, int64_t n_pts, const double* x, double* v
 /*
  * ht_eval_diff_host -- ht_eval_diff on HOST buffers of the same layouts: copies
  * x to the device, evaluates, copies val and jac back, and returns when the
- * results are in host memory.  From 8,192 points on, the points go in 2 or 8
- * column blocks over two internal streams (after the work already queued on
- * `stream`), so copies of one block overlap the evaluation of the next.
- * Uses a device workspace and two streams owned by the system (grown on
- * demand, freed with the system).  Pinned host memory gives the fastest
- * copies; pageable memory works.
+ * results are in host memory.  The points go to the device in one copy (after
+ * the work already queued on `stream`); the polynomials are then evaluated in
+ * blocks of at least 8 (at most 8 blocks) on two internal streams, and each
+ * block's rows of val and jac -- contiguous in the point-fastest layouts --
+ * go back in one copy while the next block is evaluated.  Uses a device
+ * workspace and two streams owned by the system (grown on demand, freed with
+ * the system).  Pinned host memory gives the fastest copies; pageable memory
+ * works.
  */
 int ht_eval_diff_host(ht_system* sys, int64_t n_pts, const double* x_host, double* val_host,
                       double* jac_host, void* stream);
@@ -150,6 +152,13 @@ int ht_eval_diff_unfused(ht_system* sys, int64_t n_pts, const double* x, double*
  *              radix-2^29 limbs, sums in an exact fixed-point frame per
  *              output (systems with at most 64 variables; HT_EUNSUPPORTED
  *              otherwise),
+ *            3 the three kernels of ht_eval_diff_unfused (coeff, mon, sum
+ *              over a workspace): work spread over monomials and points,
+ *              which suits few points; the first call allocates the
+ *              workspace (grown on demand, kept in the system, so the call
+ *              is not allocation-free), and results are bitwise those of
+ *              variants 0 and 1 (at most 65,535 monomials and outputs;
+ *              HT_EUNSUPPORTED otherwise),
  *           -1 default (1)
  *   threads  CTA size 64, 128 or 256, or 0 for the default (128); for
  *            variant 2, 128 (or 0, 64) runs one unit of 32 points and one
@@ -157,7 +166,7 @@ int ht_eval_diff_unfused(ht_system* sys, int64_t n_pts, const double* x, double*
  *            256 runs a block of 32 points per CTA with the block's points in
  *            shared memory and the polynomials dealt to its 8 warps (the same
  *            bits either way)
- * Variants 0 and 1 perform the same operations in the same order, so their
+ * Variants 0, 1 and 3 perform the same operations in the same order, so their
  * results are bitwise identical; variant 2 meets the same accuracy bound
  * (a small multiple of 2^(-53 L) times the sum of the moduli of the terms of
  * each output) with its own rounding.
@@ -165,7 +174,8 @@ int ht_eval_diff_unfused(ht_system* sys, int64_t n_pts, const double* x, double*
  * n <= 32: by default (and with variant 2) the tracker evaluates f on the
  * integer pipe, and for QD also solves the Newton systems there
  * (ht_mgs_solve_ex variant 2); with variant 0 or 1 it uses the FP64 pipe
- * throughout.  Double systems always track on the FP64 pipe.
+ * throughout (variant 3 counts as FP64 there).  Double systems always track
+ * on the FP64 pipe.
  */
 int ht_set_eval_config(ht_system* sys, int variant, int threads);
 

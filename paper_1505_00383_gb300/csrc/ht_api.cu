@@ -36,13 +36,20 @@ bool is_device_ptr(const void* p) {
   cudaGetDevice(&dev);
   return (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) && a.device == dev;
 }
-int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st) {
+int launch_evaldiff_range(const ht_system* s, int64_t n_pts, int j0, int j1, const double* x, double* val,
+                          double* jac, cudaStream_t st) {
   switch (s->limbs) {
-    case 1: return launch_evaldiff_l<1>(s, n_pts, x, val, jac, st);
-    case 2: return launch_evaldiff_l<2>(s, n_pts, x, val, jac, st);
-    case 4: return launch_evaldiff_l<4>(s, n_pts, x, val, jac, st);
+    case 1: return launch_evaldiff_l<1>(s, n_pts, j0, j1, x, val, jac, st);
+    case 2: return launch_evaldiff_l<2>(s, n_pts, j0, j1, x, val, jac, st);
+    case 4: return launch_evaldiff_l<4>(s, n_pts, j0, j1, x, val, jac, st);
   }
   return set_error(HT_EINVAL, "ht_eval_diff: limbs=%d", s->limbs);
+}
+int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st) {
+  // the three-kernel organisation keeps its workspace in the system, a cache
+  // that does not change what the system is
+  if (s->eval_variant == 3) return run_unfused(const_cast<ht_system*>(s), n_pts, x, val, jac, nullptr, st);
+  return launch_evaldiff_range(s, n_pts, 0, s->np, x, val, jac, st);
 }
 
 int sm_count() {
@@ -250,17 +257,26 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
   int rc = check_eval_args(s, n_pts, x_host, val_host, jac_host, false);
   if (rc != HT_OK || n_pts == 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  // Pipelined in chunks of points: two streams each copy a chunk in,
-  // evaluate it and copy it out, so one chunk's copies overlap the other's
-  // evaluation.  A chunk is a column block of the point-fastest layouts: one
-  // 2-D copy per array (rows = entries, row length = the chunk's points).
+  // Pipelined over blocks of polynomials: the points go to the device in one
+  // copy; then two streams alternate, each evaluating a block of polynomials
+  // at every point into its own slab and copying the slab back.  In the
+  // point-fastest layouts a block of polynomials is a contiguous range of
+  // val and of jac on both sides, so every copy back is one contiguous
+  // transfer, and one block's copy overlaps the next block's evaluation.
+  // Blocks hold at least 8 polynomials (the block-organised integer kernel
+  // deals polynomials to 8 warps); the three-kernel variant takes one block.
   const size_t L = s->limbs;
-  const int64_t rx = (int64_t)s->nv * 2 * L, rv = (int64_t)s->np * 2 * L, rj = (int64_t)s->np * s->nv * 2 * L;
-  const int n_chunks = n_pts >= 8 * 4096 ? 8 : (n_pts >= 2 * 4096 ? 2 : 1);
-  const int64_t C = ((n_pts + n_chunks - 1) / n_chunks + 31) / 32 * 32;
-  const int slots = n_chunks > 1 ? 2 : 1;
-  const size_t per_slot = (size_t)(rx + rv + rj) * C * 8;
-  const size_t need = per_slot * slots;
+  const int64_t rx = (int64_t)s->nv * 2 * L, rv = 2 * L, rj = (int64_t)s->nv * 2 * L;  // doubles per point per row
+  int nb = s->np;
+  if (s->eval_variant != 3) {
+    nb = (s->np + 7) / 8;
+    if (nb < 8) nb = 8;
+    if (nb > s->np) nb = s->np;
+  }
+  const int n_blocks = (s->np + nb - 1) / nb;
+  const int slots = n_blocks > 1 ? 2 : 1;
+  const size_t b_x = (size_t)rx * n_pts * 8, b_slot = (size_t)nb * (rv + rj) * n_pts * 8;
+  const size_t need = b_x + b_slot * slots;
   if (s->ws_bytes < need) {
     if (s->d_ws) {
       cudaDeviceSynchronize();
@@ -280,13 +296,16 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
       cudaError_t e = cudaStreamCreateWithFlags(&s->host_streams[k], cudaStreamNonBlocking);
       if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: stream");
     }
+  double* dx = (double*)s->d_ws;
+  cudaError_t e = cudaMemcpyAsync(dx, x_host, b_x, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copy of the points");
   cudaStream_t sts[2] = {st, st};
   cudaEvent_t ready = nullptr;
   if (slots > 1) {
     sts[0] = s->host_streams[0];
     sts[1] = s->host_streams[1];
-    cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ready, st);  // after the caller's earlier work
+    e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ready, st);  // the points (and the caller's earlier work)
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sts[0], ready, 0);
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sts[1], ready, 0);
     if (e != cudaSuccess) {
@@ -294,23 +313,17 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
       return cuda_fail(e, "ht_eval_diff_host: ordering");
     }
   }
-  cudaError_t e = cudaSuccess;
-  for (int c = 0; c < n_chunks && rc == HT_OK && e == cudaSuccess; ++c) {
-    const int64_t p0 = (int64_t)c * C;
-    if (p0 >= n_pts) break;
-    const int64_t cc = n_pts - p0 < C ? n_pts - p0 : C;
-    cudaStream_t cs = sts[c & 1];
-    char* slot = (char*)s->d_ws + per_slot * (c % slots);
-    double* dx = (double*)slot;
-    double* dv = dx + rx * cc;
-    double* dj = dv + rv * cc;
-    e = cudaMemcpy2DAsync(dx, cc * 8, x_host + p0, n_pts * 8, cc * 8, rx, cudaMemcpyHostToDevice, cs);
-    if (e != cudaSuccess) break;
-    rc = launch_evaldiff(s, cc, dx, dv, dj, cs);
+  for (int b = 0; b < n_blocks && rc == HT_OK && e == cudaSuccess; ++b) {
+    const int j0 = b * nb, j1 = j0 + nb < s->np ? j0 + nb : s->np;
+    cudaStream_t cs = sts[b & 1];
+    double* dv = (double*)((char*)s->d_ws + b_x + b_slot * (b % slots));
+    double* dj = dv + (int64_t)nb * rv * n_pts;
+    rc = s->eval_variant == 3 ? launch_evaldiff(s, n_pts, dx, dv, dj, cs)
+                              : launch_evaldiff_range(s, n_pts, j0, j1, dx, dv, dj, cs);
     if (rc != HT_OK) break;
-    e = cudaMemcpy2DAsync(val_host + p0, n_pts * 8, dv, cc * 8, cc * 8, rv, cudaMemcpyDeviceToHost, cs);
-    if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(jac_host + p0, n_pts * 8, dj, cc * 8, cc * 8, rj, cudaMemcpyDeviceToHost, cs);
+    const size_t cv = (size_t)(j1 - j0) * rv * n_pts * 8, cj = (size_t)(j1 - j0) * rj * n_pts * 8;
+    e = cudaMemcpyAsync(val_host + (int64_t)j0 * rv * n_pts, dv, cv, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(jac_host + (int64_t)j0 * rj * n_pts, dj, cj, cudaMemcpyDeviceToHost, cs);
   }
   cudaError_t e2 = cudaStreamSynchronize(sts[0]);
   if (slots > 1) {
@@ -327,7 +340,9 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
 int ht_set_eval_config(ht_system* s, int variant, int threads) {
   clear_error();
   if (!s) return set_error(HT_EINVAL, "ht_set_eval_config: NULL system");
-  if (variant < -1 || variant > 2) return set_error(HT_EINVAL, "ht_set_eval_config: variant=%d", variant);
+  if (variant < -1 || variant > 3) return set_error(HT_EINVAL, "ht_set_eval_config: variant=%d", variant);
+  if (variant == 3 && (s->M > 65535 || (int64_t)s->np * (s->nv + 1) > 65535))
+    return set_error(HT_EUNSUPPORTED, "ht_set_eval_config: the three-kernel variant takes at most 65,535 monomials and outputs");
   if (variant == 2 && s->nv > 64)
     return set_error(HT_EUNSUPPORTED, "ht_set_eval_config: the integer variant supports at most 64 variables");
   if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
@@ -347,13 +362,14 @@ int ht_tune_eval(ht_system* s, int64_t n_pts, const double* x, double* val, doub
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  const int variants[3] = {1, 0, 2}, sizes[3] = {128, 64, 256};
-  const int nvar = s->nv <= 64 ? 3 : 2;
+  const int variants[4] = {1, 0, 3, 2}, sizes[3] = {128, 64, 256};
+  const bool int_ok = s->nv <= 64, uf_ok = s->M <= 65535 && (int64_t)s->np * (s->nv + 1) <= 65535;
   float best = 1e30f;
   int bv = 1, bt = 128;
-  for (int vi = 0; vi < nvar && rc == HT_OK; ++vi)
+  for (int vi = 0; vi < 4 && rc == HT_OK; ++vi)
     for (int ti = 0; ti < 3 && rc == HT_OK; ++ti) {
-      if (variants[vi] == 2 && ti == 1) continue;  // integer limbs: 128 (per unit) or 256 (per block)
+      if (variants[vi] == 2 && (!int_ok || ti == 1)) continue;  // integer limbs: 128 (per unit) or 256 (per block)
+      if (variants[vi] == 3 && (!uf_ok || ti > 0)) continue;     // three kernels: one shape
       s->eval_variant = variants[vi];
       s->eval_threads = sizes[ti];
       rc = launch_evaldiff(s, n_pts, x, val, jac, st);  // warm-up

@@ -30,8 +30,8 @@ namespace ht {
 
 struct EvalArgs {
   PolyView v;
-  const int32_t* poly_off;
-  int nv, np;
+  const int32_t* poly_off;  // advanced to the first polynomial of the range
+  int nv, np;               // np: polynomials in the range; val and jac hold them from index 0
   double* val;
   double* jac;
   int64_t n_units;
@@ -184,19 +184,20 @@ static int launch_int(const EvalArgs& a, const ht_system* s, int threads, cudaSt
 }
 
 template <int L>
-int launch_evaldiff_l(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st) {
+int launch_evaldiff_l(const ht_system* s, int64_t n_pts, int j0, int j1, const double* x, double* val, double* jac,
+                      cudaStream_t st) {
   EvalArgs a;
   a.v.mon_off = s->d_mon_off;
   a.v.pairs = s->d_pairs;
   a.v.coef = s->d_coef;
   a.v.x = x;
   a.v.npts = n_pts;
-  a.poly_off = s->d_poly_off;
+  a.poly_off = s->d_poly_off + j0;  // polynomials j0 .. j1 - 1, written from output row 0
   a.nv = s->nv;
-  a.np = s->np;
+  a.np = j1 - j0;
   a.val = val;
   a.jac = jac;
-  a.n_units = ((n_pts + 31) / 32) * s->np;
+  a.n_units = ((n_pts + 31) / 32) * a.np;
   const int threads = s->eval_threads > 0 ? s->eval_threads : 128;
   if (s->eval_variant == 2 && s->d_coef_fz && s->nv <= kIntMaxVars && s->max_k <= 64)
     return launch_int<L>(a, s, threads, st);
@@ -207,6 +208,7 @@ int launch_evaldiff_l(const ht_system* s, int64_t n_pts, const double* x, double
 #ifndef HT_LIMBS
 #error "compile once per precision with -DHT_LIMBS=1, 2 or 4"
 #endif
-template int launch_evaldiff_l<HT_LIMBS>(const ht_system*, int64_t, const double*, double*, double*, cudaStream_t);
+template int launch_evaldiff_l<HT_LIMBS>(const ht_system*, int64_t, int, int, const double*, double*, double*,
+                                         cudaStream_t);
 
 }  // namespace ht

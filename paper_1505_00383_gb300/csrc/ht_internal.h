@@ -61,10 +61,20 @@ void clear_error();
 bool is_device_ptr(const void* p);
 int sm_count();
 
+// Polynomials j0 .. j1 - 1 at n_pts points: val and jac receive them from
+// their row 0 (val [j1 - j0][2][L][n_pts], jac [j1 - j0][nv][2][L][n_pts]).
 template <int L>
-int launch_evaldiff_l(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, cudaStream_t st);
+int launch_evaldiff_l(const ht_system* s, int64_t n_pts, int j0, int j1, const double* x, double* val, double* jac,
+                      cudaStream_t st);
+int launch_evaldiff_range(const ht_system* s, int64_t n_pts, int j0, int j1, const double* x, double* val,
+                          double* jac, cudaStream_t st);
 int launch_evaldiff(const ht_system* s, int64_t n_pts, const double* x, double* val, double* jac,
                     cudaStream_t st);
+
+// ht_eval_diff_unfused after argument checks (also ht_eval_diff with
+// variant 3); stats may be NULL (then nothing blocks).
+int run_unfused(ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, ht_unfused_stats* stats,
+                cudaStream_t st);
 
 // The three kernels of ht_eval_diff_unfused on points p0 .. p0 + cc - 1 of
 // x/val/jac (column stride n) through the workspace ws ([slots][2][L][cc]);

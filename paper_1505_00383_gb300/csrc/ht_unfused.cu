@@ -194,25 +194,12 @@ static int uf_prepare(ht_system* s) {
   return HT_OK;
 }
 
-}  // namespace ht
-
-using namespace ht;
-
-extern "C" int ht_eval_diff_unfused(ht_system* s, int64_t n_pts, const double* x, double* val, double* jac,
-                                    ht_unfused_stats* stats, void* stream) {
-  clear_error();
-  if (stats) std::memset(stats, 0, sizeof *stats);
-  if (!s) return set_error(HT_EINVAL, "ht_eval_diff_unfused: NULL system");
-  if (n_pts < 0) return set_error(HT_EINVAL, "ht_eval_diff_unfused: n_pts < 0");
-  if (n_pts == 0) return HT_OK;
-  if (!x || !val || !jac || !is_device_ptr(x) || !is_device_ptr(val) || !is_device_ptr(jac) ||
-      (((uintptr_t)x | (uintptr_t)val | (uintptr_t)jac) & 7))
-    return set_error(HT_EINVAL, "ht_eval_diff_unfused: x, val and jac must be device memory");
+int run_unfused(ht_system* s, int64_t n_pts, const double* x, double* val, double* jac, ht_unfused_stats* stats,
+                cudaStream_t st) {
   if (s->M > 65535 || (int64_t)s->np * (s->nv + 1) > 65535)
     return set_error(HT_EUNSUPPORTED, "ht_eval_diff_unfused: at most 65,535 monomials and outputs");
   int rc = uf_prepare(s);
   if (rc != HT_OK) return rc;
-  cudaStream_t st = (cudaStream_t)stream;
   const int L = s->limbs;
   // chunk of points whose workspace ([slots][2][L][chunk]) fits in 2 GiB
   const size_t per_pt = (size_t)s->uf_slots * 2 * L * sizeof(double);
@@ -279,6 +266,23 @@ extern "C" int ht_eval_diff_unfused(ht_system* s, int64_t n_pts, const double* x
     if (e != cudaSuccess) rc = cuda_fail(e, "ht_eval_diff_unfused");
   }
   return rc;
+}
+
+}  // namespace ht
+
+using namespace ht;
+
+extern "C" int ht_eval_diff_unfused(ht_system* s, int64_t n_pts, const double* x, double* val, double* jac,
+                                    ht_unfused_stats* stats, void* stream) {
+  clear_error();
+  if (stats) std::memset(stats, 0, sizeof *stats);
+  if (!s) return set_error(HT_EINVAL, "ht_eval_diff_unfused: NULL system");
+  if (n_pts < 0) return set_error(HT_EINVAL, "ht_eval_diff_unfused: n_pts < 0");
+  if (n_pts == 0) return HT_OK;
+  if (!x || !val || !jac || !is_device_ptr(x) || !is_device_ptr(val) || !is_device_ptr(jac) ||
+      (((uintptr_t)x | (uintptr_t)val | (uintptr_t)jac) & 7))
+    return set_error(HT_EINVAL, "ht_eval_diff_unfused: x, val and jac must be device memory");
+  return run_unfused(s, n_pts, x, val, jac, stats, (cudaStream_t)stream);
 }
 #else
 }  // namespace ht

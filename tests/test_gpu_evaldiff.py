@@ -112,15 +112,27 @@ def test_zero_points_is_a_noop_and_bad_args_are_rejected(ht):
         ht.ht_create_system(2, 1, [1], np.zeros((1, 2), np.int8), np.zeros((1, 2, 3)), 3)
 
 
-@pytest.mark.parametrize("L,n", [(1, 70), (4, 70), (2, 2 * 4096 + 37), (1, 8 * 4096 + 5)])
-def test_host_buffer_entry_point_matches(ht, L, n):
-    """One block, two blocks and eight blocks with a ragged last block: the
-    pipelined host entry gives the device entry's bits."""
-    s = synth.config_system("batched_n12_dd")
+@pytest.mark.parametrize("name,L,n,variant", [("batched_n12_dd", 1, 70, -1), ("batched_n12_dd", 4, 70, 2),
+                                              ("batched_n12_dd", 2, 2 * 4096 + 37, 2), ("plain_n6_d", 1, 333, -1),
+                                              ("evaldiff_n32", 1, 8 * 4096 + 5, -1), ("evaldiff_n32", 4, 1000, 2),
+                                              ("evaldiff_n32", 2, 517, 3)])
+def test_host_buffer_entry_point_matches(ht, name, L, n, variant):
+    """The host entry evaluates blocks of polynomials (12 polynomials: blocks
+    of 8 and 4; 32: four blocks of 8; 6: one block; the three-kernel variant:
+    one block) and copies each block's rows back: the device entry's bits."""
+    s = synth.config_system(name)
     x = synth.unit_points(55, s.n_vars, n, L)
-    v1, j1 = _run(ht, s, x, L)
-    v2, j2 = _run(ht, s, x, L, host=True)
-    assert np.array_equal(v1, v2) and np.array_equal(j1, j2)
+    hs = ht.system_from(s, L)
+    ht.ht_set_eval_config(hs, variant, 256 if variant == 2 else 0)
+    xd = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    v1 = torch.full((s.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    j1 = torch.full((s.n_polys, s.n_vars, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    ht.ht_eval_diff(hs, n, xd, v1, j1)
+    torch.cuda.synchronize()
+    v2 = np.full((s.n_polys, 2, L, n), np.nan)
+    j2 = np.full((s.n_polys, s.n_vars, 2, L, n), np.nan)
+    ht.ht_eval_diff_host(hs, n, np.ascontiguousarray(x), v2, j2)
+    assert np.array_equal(v1.cpu().numpy(), v2) and np.array_equal(j1.cpu().numpy(), j2)
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
@@ -323,6 +335,13 @@ def test_unfused_three_kernels_equal_the_fused_kernel(ht, name, L):
         out.append((val.cpu().numpy(), jac.cpu().numpy()))
     assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
     _check(s, x, L, out[1][0], out[1][1])
+    # the same organisation as ht_eval_diff's variant 3
+    ht.ht_set_eval_config(hs, 3, 0)
+    val = torch.full((s.n_polys, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    jac = torch.full((s.n_polys, s.n_vars, 2, L, n), np.nan, dtype=torch.float64, device="cuda")
+    ht.ht_eval_diff(hs, n, xd, val, jac)
+    torch.cuda.synchronize()
+    assert np.array_equal(val.cpu().numpy(), out[0][0]) and np.array_equal(jac.cpu().numpy(), out[0][1])
 
 
 def test_unfused_in_chunks_at_full_size(ht):
