@@ -139,7 +139,8 @@ def test_host_buffer_entry_point_matches(ht, name, L, n, variant):
 def test_every_kernel_configuration_gives_identical_results(ht, L):
     """Compact and unrolled monomial bodies, 64/128/256 threads: the same
     operations in the same order, so bitwise identical outputs; the autotuner
-    then keeps one of them."""
+    then keeps one of them (at these few points often the three kernels,
+    bitwise the same too)."""
     s = synth.config_system("evaldiff_n32")
     n = 32 * 5 + 7
     x = synth.unit_points(3 + L, s.n_vars, n, L)
@@ -160,9 +161,9 @@ def test_every_kernel_configuration_gives_identical_results(ht, L):
     val = torch.empty((s.n_polys, 2, L, n), dtype=torch.float64, device="cuda")
     jac = torch.empty((s.n_polys, s.n_vars, 2, L, n), dtype=torch.float64, device="cuda")
     v, t, ms = ht.ht_tune_eval(hs, n, xd, val, jac, reps=1)
-    assert v in (0, 1, 2) and t in (64, 128, 256) and ms > 0
-    if v in (0, 1):
-        assert np.array_equal(val.cpu().numpy(), ref[0])
+    assert v in (0, 1, 2, 3) and t in (64, 128, 256) and ms > 0
+    if v in (0, 1, 3):  # the three kernels (3) take the FP64 bodies' operations in their order
+        assert np.array_equal(val.cpu().numpy(), ref[0]) and np.array_equal(jac.cpu().numpy(), ref[1])
     else:  # the integer variant: its own arithmetic, same accuracy contract
         _check(s, x, L, val.cpu().numpy(), jac.cpu().numpy())
 
