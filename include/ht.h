@@ -102,9 +102,10 @@ int ht_eval_diff(const ht_system* sys, int64_t n_pts, const double* x, double* v
  * x to the device, evaluates, copies val and jac back, and returns when the
  * results are in host memory.  The points go to the device in one copy (after
  * the work already queued on `stream`); the polynomials are then evaluated in
- * blocks of at least 8 (at most 8 blocks) on two internal streams, and each
+ * blocks of at least 8 (at most 8 blocks) on one internal stream into up to
+ * three device slabs, and a second internal stream copies each finished
  * block's rows of val and jac -- contiguous in the point-fastest layouts --
- * go back in one copy while the next block is evaluated.  Uses a device
+ * back in one transfer while the next blocks are evaluated.  Uses a device
  * workspace and two streams owned by the system (grown on demand, freed with
  * the system).  Pinned host memory gives the fastest copies; pageable memory
  * works.

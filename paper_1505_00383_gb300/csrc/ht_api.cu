@@ -258,13 +258,16 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
   if (rc != HT_OK || n_pts == 0) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   // Pipelined over blocks of polynomials: the points go to the device in one
-  // copy; then two streams alternate, each evaluating a block of polynomials
-  // at every point into its own slab and copying the slab back.  In the
+  // copy; then one stream evaluates the blocks, each into one of up to three
+  // slabs, while a second stream copies every finished slab back.  In the
   // point-fastest layouts a block of polynomials is a contiguous range of
   // val and of jac on both sides, so every copy back is one contiguous
-  // transfer, and one block's copy overlaps the next block's evaluation.
-  // Blocks hold at least 8 polynomials (the block-organised integer kernel
-  // deals polynomials to 8 warps); the three-kernel variant takes one block.
+  // transfer.  Events order the two streams: a slab's copy waits for its
+  // evaluation, and the evaluation that reuses a slab waits for that slab's
+  // previous copy, so the evaluations never wait for a copy still in flight
+  // unless three are.  Blocks hold at least 8 polynomials (the
+  // block-organised integer kernel deals polynomials to 8 warps); the
+  // three-kernel variant takes one block.
   const size_t L = s->limbs;
   const int64_t rx = (int64_t)s->nv * 2 * L, rv = 2 * L, rj = (int64_t)s->nv * 2 * L;  // doubles per point per row
   int nb = s->np;
@@ -274,7 +277,7 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
     if (nb > s->np) nb = s->np;
   }
   const int n_blocks = (s->np + nb - 1) / nb;
-  const int slots = n_blocks > 1 ? 2 : 1;
+  const int slots = n_blocks < 3 ? n_blocks : 3;
   const size_t b_x = (size_t)rx * n_pts * 8, b_slot = (size_t)nb * (rv + rj) * n_pts * 8;
   const size_t need = b_x + b_slot * slots;
   if (s->ws_bytes < need) {
@@ -291,48 +294,42 @@ int ht_eval_diff_host(ht_system* s, int64_t n_pts, const double* x_host, double*
     }
     s->ws_bytes = need;
   }
-  for (int k = 0; k < 2 && slots > 1; ++k)
+  for (int k = 0; k < 2; ++k)
     if (!s->host_streams[k]) {
       cudaError_t e = cudaStreamCreateWithFlags(&s->host_streams[k], cudaStreamNonBlocking);
       if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: stream");
     }
+  cudaStream_t comp = s->host_streams[0], copy = s->host_streams[1];
+  cudaEvent_t ev[7] = {};  // [0] ordering after the caller's stream, [1..3] evaluated, [4..6] copied
+  cudaError_t e = cudaSuccess;
+  for (int k = 0; k < 7 && e == cudaSuccess; ++k) e = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(ev[0], st);  // after the work already queued by the caller
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(comp, ev[0], 0);
   double* dx = (double*)s->d_ws;
-  cudaError_t e = cudaMemcpyAsync(dx, x_host, b_x, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copy of the points");
-  cudaStream_t sts[2] = {st, st};
-  cudaEvent_t ready = nullptr;
-  if (slots > 1) {
-    sts[0] = s->host_streams[0];
-    sts[1] = s->host_streams[1];
-    e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ready, st);  // the points (and the caller's earlier work)
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(sts[0], ready, 0);
-    if (e == cudaSuccess) e = cudaStreamWaitEvent(sts[1], ready, 0);
-    if (e != cudaSuccess) {
-      if (ready) cudaEventDestroy(ready);
-      return cuda_fail(e, "ht_eval_diff_host: ordering");
-    }
-  }
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dx, x_host, b_x, cudaMemcpyHostToDevice, comp);
   for (int b = 0; b < n_blocks && rc == HT_OK && e == cudaSuccess; ++b) {
-    const int j0 = b * nb, j1 = j0 + nb < s->np ? j0 + nb : s->np;
-    cudaStream_t cs = sts[b & 1];
-    double* dv = (double*)((char*)s->d_ws + b_x + b_slot * (b % slots));
+    const int j0 = b * nb, j1 = j0 + nb < s->np ? j0 + nb : s->np, k = b % slots;
+    double* dv = (double*)((char*)s->d_ws + b_x + b_slot * k);
     double* dj = dv + (int64_t)nb * rv * n_pts;
-    rc = s->eval_variant == 3 ? launch_evaldiff(s, n_pts, dx, dv, dj, cs)
-                              : launch_evaldiff_range(s, n_pts, j0, j1, dx, dv, dj, cs);
+    if (b >= slots) e = cudaStreamWaitEvent(comp, ev[4 + k], 0);  // the slab's previous copy is done
+    if (e != cudaSuccess) break;
+    rc = s->eval_variant == 3 ? launch_evaldiff(s, n_pts, dx, dv, dj, comp)
+                              : launch_evaldiff_range(s, n_pts, j0, j1, dx, dv, dj, comp);
     if (rc != HT_OK) break;
+    e = cudaEventRecord(ev[1 + k], comp);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(copy, ev[1 + k], 0);
     const size_t cv = (size_t)(j1 - j0) * rv * n_pts * 8, cj = (size_t)(j1 - j0) * rj * n_pts * 8;
-    e = cudaMemcpyAsync(val_host + (int64_t)j0 * rv * n_pts, dv, cv, cudaMemcpyDeviceToHost, cs);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(jac_host + (int64_t)j0 * rj * n_pts, dj, cj, cudaMemcpyDeviceToHost, cs);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(val_host + (int64_t)j0 * rv * n_pts, dv, cv, cudaMemcpyDeviceToHost, copy);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(jac_host + (int64_t)j0 * rj * n_pts, dj, cj, cudaMemcpyDeviceToHost, copy);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4 + k], copy);
   }
-  cudaError_t e2 = cudaStreamSynchronize(sts[0]);
-  if (slots > 1) {
-    cudaError_t e3 = cudaStreamSynchronize(sts[1]);
-    if (e2 == cudaSuccess) e2 = e3;
-    cudaEventDestroy(ready);
-  }
+  cudaError_t e2 = cudaStreamSynchronize(comp);
+  cudaError_t e3 = cudaStreamSynchronize(copy);
+  for (auto& x : ev)
+    if (x) cudaEventDestroy(x);
   if (rc != HT_OK) return rc;
-  if (e == cudaSuccess) e = e2;
+  if (e == cudaSuccess) e = e2 != cudaSuccess ? e2 : e3;
   if (e != cudaSuccess) return cuda_fail(e, "ht_eval_diff_host: copies");
   return HT_OK;
 }

@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(128, 4) evaldiff_int_kernel(EvalArgs a, const 
     int_point<L>(a.v.x, a.nv, n, p, X, lg);
     double vre[L], vim[L];
     int_row<L>(a.v.mon_off, a.v.pairs, cfz, clg, a.poly_off[j], a.poly_off[j + 1], X, lg, a.nv,
-               a.jac + (int64_t)j * plane, a.val, j, n, p, vre, vim, P);
+               a.jac + (int64_t)j * plane, n, p, vre, vim, P);
 #pragma unroll
     for (int l = 0; l < L; ++l) {
       a.val[((int64_t)(j * 2) * L + l) * n + p] = vre[l];
@@ -146,7 +146,7 @@ __global__ void __launch_bounds__(256, 2) evaldiff_intblk_kernel(EvalArgs a, con
     for (int j = warp; j < a.np; j += T) {
       double vre[L], vim[L];
       int_row<L>(a.v.mon_off, a.v.pairs, cfz, clg, a.poly_off[j], a.poly_off[j + 1], X, lg, a.nv,
-                 a.jac + (int64_t)j * plane, a.val, j, n, p, vre, vim, P);
+                 a.jac + (int64_t)j * plane, n, p, vre, vim, P);
 #pragma unroll
       for (int l = 0; l < L; ++l) {
         a.val[((int64_t)(j * 2) * L + l) * n + p] = vre[l];

@@ -36,23 +36,36 @@ __device__ __forceinline__ void st_fix(double* jrow, int64_t i, int64_t n, int64
   }
 }
 
-// The Jacobian row accumulates in place in the output slots, and the value
-// in its own slot (entry vidx of vrow, same layout): var < 0 is the value,
-// so the sweep's one accumulation site serves both.
+// The Jacobian row accumulates in place in the output slots and the value in
+// registers (vr, vi): var < 0 is the value, so the sweep's one accumulation
+// site serves both.
 template <int L>
 struct RowAcc {
+  static constexpr int WA = IntW<L>::WA;
   double* jrow;
-  double* vrow;
-  int64_t vidx;
   int64_t n, p;
+  int32_t vr[WA], vi[WA];
   __device__ __forceinline__ void add(int v, const mpi::fz<IntW<L>::W>& d, int e, int F) {
-    constexpr int WA = IntW<L>::WA;
-    double* base = v < 0 ? vrow : jrow;
-    const int64_t idx = v < 0 ? vidx : v;
     int32_t ar[WA], ai[WA];
-    ld_fix<L>(base, idx, n, p, ar, ai);
+    if (v < 0) {
+#pragma unroll
+      for (int k = 0; k < WA; ++k) {
+        ar[k] = vr[k];
+        ai[k] = vi[k];
+      }
+    } else {
+      ld_fix<L>(jrow, v, n, p, ar, ai);
+    }
     mpi::acc_add_fast<IntW<L>::W, WA>(ar, ai, d, e, F);
-    st_fix<L>(base, idx, n, p, ar, ai);
+    if (v < 0) {
+#pragma unroll
+      for (int k = 0; k < WA; ++k) {
+        vr[k] = ar[k];
+        vi[k] = ai[k];
+      }
+    } else {
+      st_fix<L>(jrow, v, n, p, ar, ai);
+    }
   }
 };
 
@@ -75,29 +88,27 @@ __device__ __forceinline__ void int_point(const double* __restrict__ x, int nv, 
 
 // Monomials m0..m1 of one polynomial at the lane's point: the value as L
 // doubles per component (vre, vim) and the gradient written as doubles into
-// jrow ([nv][2][L][n], entry i at point p).  The value's fixed-point
-// accumulator lives in entry vidx of vrow (same layout; the caller's output
-// slot or a free column) while the sweep runs.  X and lg are indexable by
+// jrow ([nv][2][L][n], entry i at point p).  X and lg are indexable by
 // variable (local arrays or shared-memory views); P is scratch for the
 // forward products (max monomial size entries).
 template <int L, class XA, class LG>
 __device__ void int_row(const int32_t* __restrict__ mon_off, const uint16_t* __restrict__ pairs,
                         const mpi::fz<IntW<L>::W>* __restrict__ cfz, const float* __restrict__ clg, int m0, int m1,
-                        const XA& X, const LG& lg, int nv, double* jrow, double* vrow, int64_t vidx, int64_t n,
-                        int64_t p, double* vre, double* vim, mpi::fz<IntW<L>::W>* P) {
+                        const XA& X, const LG& lg, int nv, double* jrow, int64_t n, int64_t p, double* vre,
+                        double* vim, mpi::fz<IntW<L>::W>* P) {
   constexpr int WA = IntW<L>::WA;
   int Fv[kIntMaxVars];
   const int F = mpi::frames_for_poly<WA>(mon_off, pairs, clg, m0, m1, lg, nv, Fv);
-  int32_t vr[WA], vi[WA];
+  RowAcc<L> acc;
+  acc.jrow = jrow;
+  acc.n = n;
+  acc.p = p;
 #pragma unroll
-  for (int k = 0; k < WA; ++k) vr[k] = vi[k] = 0;
-  for (int i = 0; i < nv; ++i) st_fix<L>(jrow, i, n, p, vr, vi);
-  st_fix<L>(vrow, vidx, n, p, vr, vi);
-  RowAcc<L> acc{jrow, vrow, vidx, n, p};
+  for (int k = 0; k < WA; ++k) acc.vr[k] = acc.vi[k] = 0;
+  for (int i = 0; i < nv; ++i) st_fix<L>(jrow, i, n, p, acc.vr, acc.vi);
   for (int m = m0; m < m1; ++m) mpi::sweep_monomial<L>(mon_off, pairs, cfz, m, X, Fv, F, acc, P);
-  ld_fix<L>(vrow, vidx, n, p, vr, vi);
-  mpi::fixed_to_doubles<WA, L>(vr, F, vre);
-  mpi::fixed_to_doubles<WA, L>(vi, F, vim);
+  mpi::fixed_to_doubles<WA, L>(acc.vr, F, vre);
+  mpi::fixed_to_doubles<WA, L>(acc.vi, F, vim);
   double o[L];
   for (int i = 0; i < nv; ++i) {
     int32_t ar[WA], ai[WA];

@@ -649,9 +649,8 @@ __global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kern
           cx<L> fj;
           if constexpr (INT) {
             double vre[L], vim[L];
-            // the value accumulates in column n of the row, which -h fills afterwards
             int_row<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
-                       __ldg(a.poly_off + j + 1), X, lg, n, Arow, Arow, n, m, p, vre, vim, P);
+                       __ldg(a.poly_off + j + 1), X, lg, n, Arow, m, p, vre, vim, P);
             fj = cx_from<L>(vre, vim);
           } else {
             fj = eval_poly<L>(v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), n, p, Arow);
