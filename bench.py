@@ -275,7 +275,7 @@ def _agreement(A, B, tol=1e-10):
     return min(fr)
 
 
-def unfused_ablation(ht, torch, stream, flush, system, xs, n, fused_ms):
+def unfused_ablation(ht, torch, stream, flush, system, xs, n, fused_ms, fused_fp64_ms):
     """The paper's three-kernel organisation (coeff, mon, sum over a vertical
     workspace; Section 3, Tables tabcpugpu and tabmemory) against the fused
     kernel on the same points: per precision one timed call after a warm-up,
@@ -298,7 +298,9 @@ def unfused_ablation(ht, torch, stream, flush, system, xs, n, fused_ms):
             "GB_per_s": {k: d["bytes_" + k] / (d["ms_" + k] * 1e-3) / 1e9 for k in ("coeff", "mon", "sum")},
             "workspace_GB_moved": (d["bytes_coeff"] + d["bytes_mon"] + d["bytes_sum"]) / 1e9,
             "fused_ms": fused_ms[L], "fused_variant": "the benchmark's tuned kernel",
-            "unfused_over_fused": tot / fused_ms[L]}
+            "unfused_over_fused": tot / fused_ms[L],
+            "fused_fp64_ms": fused_fp64_ms.get(L, fused_ms[L]),
+            "unfused_over_fused_same_arithmetic": tot / fused_fp64_ms.get(L, fused_ms[L])}
         del val, jac
     return out
 
@@ -709,7 +711,7 @@ def run_ours(a):
     ablation = None
     if not a.no_ablation:
         ablation = unfused_ablation(ht, torch, stream, flush, system, xs, n,
-                                    {L: statistics.mean(launch_ms[L]) for L in PRECISIONS})
+                                    {L: statistics.mean(launch_ms[L]) for L in PRECISIONS}, fp64_ref)
     paper_sweep = None
     if not a.no_paper_sweep:
         paper_sweep = paper_shape_sweep(ht, torch, stream, flush, fp64_peak, imad_peak)

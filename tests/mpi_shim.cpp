@@ -110,20 +110,38 @@ static int64_t compare_acc(int64_t n, const double* in, int smin, int smax) {
   int64_t worst = 0;
   for (int64_t q = 0; q < n; ++q) {
     fz<W> z0 = from_doubles<W, L>(in + q * 2 * L, in + q * 2 * L + L);
-    fz<W> z1 = z0;  // same value up to the dropped low limb, top limb zero
+    fz<W> z1 = z0;  // same value up to the dropped low limb, one limb down
     for (int k = 0; k + 1 < W; ++k) {
       z1.r[k] = z0.r[k + 1];
       z1.i[k] = z0.i[k + 1];
     }
-    z1.r[W - 1] = z0.r[W - 1] < 0 ? -1 : 0;  // keep the sign as a borrow
+    // the old top limb is signed; below the top a limb lies in [0, 2^29), so
+    // a negative top moves down as its two's complement digit and the new top
+    // carries the sign (-1)
+    z1.r[W - 2] = z0.r[W - 1] & MASK;
+    z1.i[W - 2] = z0.i[W - 1] & MASK;
+    z1.r[W - 1] = z0.r[W - 1] < 0 ? -1 : 0;
     z1.i[W - 1] = z0.i[W - 1] < 0 ? -1 : 0;
     z1.f = z0.f + RB;
     for (int s = smin; s <= smax; ++s) {
       const fz<W>& z = s < 0 ? z1 : z0;
+      const int F = z.f + s;
+      // the fast routine's precondition: 3 |z| < 2^(29 (WA - 1) + 28 + F);
+      // skip the frames it excludes (for DD, WA = W - 1, every s < 0)
+      int top = -1;
+      for (int k = W - 1; k >= 0 && top < 0; --k)
+        if (z.r[k] != 0 || z.i[k] != 0) top = k;
+      if (top >= 0) {
+        const int64_t mr = z.r[top] < 0 ? -(int64_t)z.r[top] : z.r[top];
+        const int64_t mi = z.i[top] < 0 ? -(int64_t)z.i[top] : z.i[top];
+        int b = 0;
+        while (((mr > mi ? mr : mi) >> b) != 0) ++b;
+        const int bits = z.f + RB * top + b + 2 + 1;  // bit length of 3 |z|, bound from above
+        if (bits > RB * (WA - 1) + 28 + F) continue;
+      }
       int32_t a1[WA] = {0}, b1[WA] = {0}, a2[WA] = {0}, b2[WA] = {0};
       a1[0] = a2[0] = 12345;
       b1[WA - 1] = b2[WA - 1] = -7;
-      const int F = z.f + s;
       acc_add<W, WA>(a1, b1, z, 3, F);
       acc_add_fast<W, WA>(a2, b2, z, 3, F);
       // exact difference of the values, limb by limb from the top (it is small)
@@ -132,7 +150,10 @@ static int64_t compare_acc(int64_t n, const double* in, int smin, int smax) {
         dr = dr * (long double)(1 << RB) + (long double)(a1[k] - a2[k]);
         di = di * (long double)(1 << RB) + (long double)(b1[k] - b2[k]);
       }
-      int64_t m = (int64_t)(dr < 0 ? -dr : dr), mi = (int64_t)(di < 0 ? -di : di);
+      // a difference beyond int64 is reported as such (no overflowing cast)
+      const long double big = 9.0e18L;
+      const long double adr = dr < 0 ? -dr : dr, adi = di < 0 ? -di : di;
+      const int64_t m = adr >= big ? INT64_MAX : (int64_t)adr, mi = adi >= big ? INT64_MAX : (int64_t)adi;
       if (m > worst) worst = m;
       if (mi > worst) worst = mi;
     }

@@ -120,7 +120,9 @@ def test_fixed_point_sums_with_cancellation(oracle_lib, shim, L, fast):
 def test_shift_accumulation_equals_generic(shim, L):
     """The single-shift accumulation gives the same limbs as the generic
     per-limb one for right and left shifts (frames slightly above the
-    accumulator's included)."""
+    accumulator's included) wherever its precondition holds: the term times
+    its factor below the top limb's bit 28 (for DD, whose accumulator has one
+    limb fewer than a term, that rules out every left shift)."""
     shim.mpi_compare_acc.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
     shim.mpi_compare_acc.restype = ctypes.c_int64
     x = _complex(77 + L, 200, L, spread=3)
