@@ -290,25 +290,29 @@ template <int L>
 __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
                          int warp, int T, int nrhs = 1, double* x2 = nullptr) {
   const int W = cols + nrhs;
-  rl<L> nrm_next = r_from<L>(0.0);
-  if (warp == 0 && act) {
+  // normalise column q (its squared norm given): a_q <- a_q / r_qq, R[q][q] = 1 / r_qq
+  auto normalise = [&](int q, rl<L> nrm) {
+    rl<L> rqq = r_sqrt(nrm);
+    rl<L> inv = r_div(r_from<L>(1.0), rqq);
+    for (int i = 0; i < rows; ++i) {
+      int64_t e = (int64_t)i * W + q;
+      st<L>(A, e, m, p, cscale_r(ld<L>(A, e, m, p), inv));
+    }
+    cx<L> rv = czero<L>();
+    rv.re = inv;
+    st<L>(R, (int64_t)q * W + q, m, p, rv);
+  };
+  if (warp == 0 && act) {  // column 0 by its owner
     rl<L> s = r_from<L>(0.0);
     for (int i = 0; i < rows; ++i) s = acc_abs2<L>(s, ld<L>(A, (int64_t)i * W, m, p));
-    nrm_next = s;
+    normalise(0, s);
   }
+  __syncthreads();
+  // Look-ahead: in the phase that projects the later columns on q_q, the
+  // owner of column q + 1 projects it first and normalises it at once, while
+  // the other warps project their columns; one barrier per column.  Every
+  // column sees the same operations in the same order as without look-ahead.
   for (int q = 0; q < cols; ++q) {
-    if (warp == q % T && act) {
-      rl<L> rqq = r_sqrt(nrm_next);
-      rl<L> inv = r_div(r_from<L>(1.0), rqq);
-      for (int i = 0; i < rows; ++i) {
-        int64_t e = (int64_t)i * W + q;
-        st<L>(A, e, m, p, cscale_r(ld<L>(A, e, m, p), inv));
-      }
-      cx<L> rv = czero<L>();
-      rv.re = inv;
-      st<L>(R, (int64_t)q * W + q, m, p, rv);
-    }
-    __syncthreads();
     int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
     for (int j = j0; j < W; j += T) {
       if (!act) continue;
@@ -323,7 +327,7 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
         st<L>(A, e, m, p, v);
         if (j == q + 1) s = acc_abs2<L>(s, v);
       }
-      if (j == q + 1) nrm_next = s;  // the owner of column q + 1 normalises it next
+      if (j == q + 1 && j < cols) normalise(j, s);  // the next pivot column, ready for the next phase
     }
     __syncthreads();
   }
@@ -376,15 +380,21 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
   using Z = mpi::fz<W>;
   const int Wc = cols + nrhs;
   Z Q[N], col[N], S[N + 1];
+  // normalise the column held in v[] as column q: stored scaled by 1/r_qq, R[q][q] = 1/r_qq
+  auto normalise = [&](int q, Z* v) {
+    const Z nrm = mpi::norm2<W, N>(v, rows, S);
+    const Z inv = mpi::inv_sqrt<W>(nrm, mpi::inv_sqrt_steps<W>());
+    for (int i = 0; i < rows; ++i) stz<L>(A, (int64_t)i * Wc + q, m, p, mpi::mul<W>(v[i], inv));
+    stz<L>(R, (int64_t)q * Wc + q, m, p, inv);
+  };
+  if (warp == 0 && act) {  // column 0 by its owner
+    for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc, m, p);
+    normalise(0, Q);
+  }
+  __syncthreads();
+  // Look-ahead as in mgs_team: the owner of column q + 1 projects it first
+  // and normalises it from the registers at once; one barrier per column.
   for (int q = 0; q < cols; ++q) {
-    if (warp == q % T && act) {
-      for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc + q, m, p);
-      const Z nrm = mpi::norm2<W, N>(Q, rows, S);
-      const Z inv = mpi::inv_sqrt<W>(nrm, mpi::inv_sqrt_steps<W>());
-      for (int i = 0; i < rows; ++i) stz<L>(A, (int64_t)i * Wc + q, m, p, mpi::mul<W>(Q[i], inv));
-      stz<L>(R, (int64_t)q * Wc + q, m, p, inv);
-    }
-    __syncthreads();
     const int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
     if (act && j0 < Wc) {
       for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc + q, m, p);
@@ -394,6 +404,12 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
         stz<L>(R, (int64_t)q * Wc + j, m, p, r);
         mpi::sub_scaled<W>(col, r, Q, rows);
         for (int i = 0; i < rows; ++i) stz<L>(A, (int64_t)i * Wc + j, m, p, col[i]);
+        if (j == q + 1 && j < cols) {
+          // the pivot column from its stored values, as the owner's reload
+          // would give: the limb strings of the doubles just written
+          for (int i = 0; i < rows; ++i) col[i] = ldz<L>(A, (int64_t)i * Wc + j, m, p);
+          normalise(j, col);
+        }
       }
     }
     __syncthreads();

@@ -5,7 +5,7 @@
 WORKLOAD is a tracking workload of synth.CONFIGS (plain_n6_d, batched_n12_dd,
 learned_n16_d, stress_n10_qd); the first M paths of its total-degree homotopy
 are tracked with the plain step rule through ht_track_paths_ex in L limbs
-(default: the workload's precision).  Used as the command of the tracker
+(default: the workload's precision) with the chosen predictor.  Used as the command of the tracker
 profiles; every step runs in libht.so.
 """
 from __future__ import annotations
@@ -28,6 +28,7 @@ def main(argv=None):
     p.add_argument("--paths", type=int, default=0, help="first M paths (0: all, the Bezout number)")
     p.add_argument("--limbs", type=int, default=0, help="1, 2 or 4 (0: the workload's)")
     p.add_argument("--h-min", type=float, default=1e-9)
+    p.add_argument("--predictor", type=int, default=0, help="0 extrapolation, 1 Euler, 2 cubic Hermite")
     a = p.parse_args(argv)
     import numpy as np
     import torch
@@ -41,8 +42,8 @@ def main(argv=None):
     st = torch.empty((m,), dtype=torch.int8, device="cuda")
     t = torch.empty((m,), dtype=torch.float64, device="cuda")
     stats = ht.ht_stats()
-    ht.ht_track_paths_ex(hs, s.degrees(), gam, m, 0, None, ht.ht_default_params(L, h_min=a.h_min), x, st, t, None,
-                         stats, None)
+    prm = ht.ht_default_params(L, h_min=a.h_min, predictor=a.predictor)
+    ht.ht_track_paths_ex(hs, s.degrees(), gam, m, 0, None, prm, x, st, t, None, stats, None)
     torch.cuda.synchronize()
     print(json.dumps(dict(workload=a.workload, limbs=L, paths=m, **stats.as_dict())))
 
