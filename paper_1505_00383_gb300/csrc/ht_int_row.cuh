@@ -36,36 +36,17 @@ __device__ __forceinline__ void st_fix(double* jrow, int64_t i, int64_t n, int64
   }
 }
 
-// The Jacobian row accumulates in place in the output slots and the value in
-// registers (vr, vi): var < 0 is the value, so the sweep's one accumulation
-// site serves both.
+// The Jacobian row accumulates in place in the output slots.
 template <int L>
 struct RowAcc {
-  static constexpr int WA = IntW<L>::WA;
   double* jrow;
   int64_t n, p;
-  int32_t vr[WA], vi[WA];
   __device__ __forceinline__ void add(int v, const mpi::fz<IntW<L>::W>& d, int e, int F) {
+    constexpr int WA = IntW<L>::WA;
     int32_t ar[WA], ai[WA];
-    if (v < 0) {
-#pragma unroll
-      for (int k = 0; k < WA; ++k) {
-        ar[k] = vr[k];
-        ai[k] = vi[k];
-      }
-    } else {
-      ld_fix<L>(jrow, v, n, p, ar, ai);
-    }
+    ld_fix<L>(jrow, v, n, p, ar, ai);
     mpi::acc_add_fast<IntW<L>::W, WA>(ar, ai, d, e, F);
-    if (v < 0) {
-#pragma unroll
-      for (int k = 0; k < WA; ++k) {
-        vr[k] = ar[k];
-        vi[k] = ai[k];
-      }
-    } else {
-      st_fix<L>(jrow, v, n, p, ar, ai);
-    }
+    st_fix<L>(jrow, v, n, p, ar, ai);
   }
 };
 
@@ -99,16 +80,14 @@ __device__ void int_row(const int32_t* __restrict__ mon_off, const uint16_t* __r
   constexpr int WA = IntW<L>::WA;
   int Fv[kIntMaxVars];
   const int F = mpi::frames_for_poly<WA>(mon_off, pairs, clg, m0, m1, lg, nv, Fv);
-  RowAcc<L> acc;
-  acc.jrow = jrow;
-  acc.n = n;
-  acc.p = p;
+  int32_t vr[WA], vi[WA];
 #pragma unroll
-  for (int k = 0; k < WA; ++k) acc.vr[k] = acc.vi[k] = 0;
-  for (int i = 0; i < nv; ++i) st_fix<L>(jrow, i, n, p, acc.vr, acc.vi);
-  for (int m = m0; m < m1; ++m) mpi::sweep_monomial<L>(mon_off, pairs, cfz, m, X, Fv, F, acc, P);
-  mpi::fixed_to_doubles<WA, L>(acc.vr, F, vre);
-  mpi::fixed_to_doubles<WA, L>(acc.vi, F, vim);
+  for (int k = 0; k < WA; ++k) vr[k] = vi[k] = 0;
+  for (int i = 0; i < nv; ++i) st_fix<L>(jrow, i, n, p, vr, vi);
+  RowAcc<L> acc{jrow, n, p};
+  mpi::eval_poly_int<L>(mon_off, pairs, cfz, m0, m1, X, F, Fv, acc, vr, vi, P);
+  mpi::fixed_to_doubles<WA, L>(vr, F, vre);
+  mpi::fixed_to_doubles<WA, L>(vi, F, vim);
   double o[L];
   for (int i = 0; i < nv; ++i) {
     int32_t ar[WA], ai[WA];

@@ -73,40 +73,41 @@ HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const f
   return frame_of<WA>(E, cnt);
 }
 
-// Value and gradient of monomial m at the point X (converted variables),
-// through one accumulation site: acc.add(var, d, e, frame) adds e d to the
-// derivative by x_var in frame Fv[var], and acc.add(-1, value, 1, Fval) the
-// monomial's value to the polynomial's value in its frame Fval.  P is scratch
+// Value (through val_add(term)) and gradient (through acc.add(var, d, e,
+// Fv[var])) of monomial m at the point X (converted variables); P is scratch
 // for k forward products.
 //
 // The reverse-mode sweep of one monomial c x_{v_0}^{a_0} ... x_{v_{k-1}}^{a_{k-1}}
 // is a sequence of steps, each at most one product followed by one action:
 //   common factor  cf <- cf x_{v_r}              (a_r - 1 times for each r)
-//   forward        P_r <- (r ? P_{r-1} : cf) x_{v_r}
-//   value          value += P_{k-1}                (cf for k = 0)
+//   forward        P_r <- (r ? P_{r-1} : cf) x_{v_r};  value += P_{k-1}
 //   backward       d_{k-1} = P_{k-2}; S = x_{v_{k-1}};
 //                  for r = k-2 .. 1: d_r = P_{r-1} S, S <- S x_{v_r};
 //                  d_0 = cf S                     (k = 1: d_0 = cf)
-// with every d_r added into the row as a_r d_r.  The loop runs the steps of
-// a monomial through a single product site and a single accumulation site,
-// so the multi-limb product (several hundred instructions for the 8-limb
-// format) and the fixed-point accumulation are each emitted once, and their
-// operands stay in registers.
-template <int L, class XA, class Acc>
+// with every d_r added into the row as a_r d_r (acc.add) and the value through
+// val_add.  The loop runs the steps of a monomial through a single product
+// and a single accumulation site, so the multi-limb product is emitted once
+// (the 8-limb product is several hundred instructions) and its operands stay
+// in registers.
+template <int L, class XA, class Acc, class ValAdd>
 HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m,
-                          const XA& X, const int* Fv, int Fval, Acc& acc, fz<IntW<L>::W>* P) {
+                          const XA& X, const int* Fv, Acc& acc, ValAdd& val_add, fz<IntW<L>::W>* P) {
   constexpr int W = IntW<L>::W;
   using Z = fz<W>;
-  enum : int { CHAIN, FWD, VAL, BWD0, BWD_D, BWD_S, LAST, DONE };
+  enum : int { CHAIN, FWD, BWD0, BWD_D, BWD_S, LAST, DONE };
   const int beg = mon_off[m], k = mon_off[m + 1] - beg;
   const uint16_t* pr = pairs + beg;
   Z cf = cfz[m], S = cf;
-  int phase = k == 0 ? VAL : CHAIN, r = 0, e = 1;
+  if (k == 0) {
+    val_add(cf);
+    return;
+  }
+  int phase = CHAIN, r = 0, e = 1;
   while (phase != DONE) {
     // the step: operands, whether to multiply, and the action
     Z lhs, rhs;
     bool prod = true;
-    int act = 0;  // 0 cf, 1 P[r], 2 S, 3 accumulate into var (-1: the value)
+    int act = 0;  // 0 cf, 1 P[r] (+ value at r = k - 1), 2 S, 3 row entry of var
     int var = 0, ex = 1;
     if (phase == CHAIN) {
       while (r < k && e >= (pr[r] >> 8)) {  // next variable with exponent left
@@ -126,11 +127,6 @@ HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const f
       lhs = r == 0 ? cf : P[r - 1];
       rhs = X[pr[r] & 0xff];
       act = 1;
-    } else if (phase == VAL) {  // the monomial's value
-      lhs = k == 0 ? cf : P[k - 1];
-      prod = false;
-      act = 3;
-      var = -1;
     } else if (phase == BWD0) {  // d_{k-1} = P_{k-2} (k >= 2) or d_0 = cf (k = 1)
       lhs = k == 1 ? cf : P[k - 2];
       prod = false;
@@ -159,16 +155,15 @@ HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const f
       cf = t;
     } else if (act == 1) {
       P[r] = t;
+      if (r == k - 1) val_add(t);
     } else if (act == 2) {
       S = t;
     } else {
-      acc.add(var, t, ex, var < 0 ? Fval : Fv[var]);
+      acc.add(var, t, ex, Fv[var]);
     }
     // next step
     if (phase == FWD) {
-      if (++r == k) phase = VAL;
-    } else if (phase == VAL) {
-      phase = k == 0 ? DONE : BWD0;
+      if (++r == k) phase = BWD0;
     } else if (phase == BWD0) {
       if (k == 1) {
         phase = DONE;
@@ -195,27 +190,16 @@ HT_HD int sweep_products(const uint16_t* pr, int k) {
   return k == 0 ? 0 : c + (k == 1 ? 1 : 3 * k - 3);
 }
 
-// Value (fixed-point vr, vi in frame F) and gradient (through acc) of the
-// monomials m0..m1.  X is anything indexable by variable that yields the
-// converted limb string (a local array, or a view of shared memory).
-template <int L, class Acc>
-struct ValueInto {  // value terms into vr, vi; derivatives to the row's acc
-  Acc& row;
-  int32_t* vr;
-  int32_t* vi;
-  HT_HD void add(int var, const fz<IntW<L>::W>& d, int e, int F) {
-    if (var < 0)
-      acc_add_fast<IntW<L>::W, IntW<L>::WA>(vr, vi, d, e, F);
-    else
-      row.add(var, d, e, F);
-  }
-};
+// Value (fixed-point vr, vi in frame F) and gradient of the monomials m0..m1.
+// X is anything indexable by variable that yields the converted limb string
+// (a local array, or a view of shared memory).
 template <int L, class XA, class Acc>
 HT_HD void eval_poly_int(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m0, int m1,
                          const XA& X, int F, const int* Fv, Acc& acc, int32_t* vr, int32_t* vi,
                          fz<IntW<L>::W>* P) {
-  ValueInto<L, Acc> both{acc, vr, vi};
-  for (int m = m0; m < m1; ++m) sweep_monomial<L>(mon_off, pairs, cfz, m, X, Fv, F, both, P);
+  constexpr int W = IntW<L>::W, WA = IntW<L>::WA;
+  auto val_add = [&](const fz<W>& t) { acc_add_fast<W, WA>(vr, vi, t, 1, F); };
+  for (int m = m0; m < m1; ++m) sweep_monomial<L>(mon_off, pairs, cfz, m, X, Fv, acc, val_add, P);
 }
 
 }  // namespace mpi
