@@ -189,8 +189,8 @@ def _kernel_sha():
 
 
 # bounded oracle samples of the tracking workloads (first paths of the system
-# the GPU tracks; about 5-15 s each on the host cores)
-ORACLE_TRACK_SAMPLE = {"plain_n6_d": 64, "batched_n12_dd": 32, "learned_n16_d": 2048, "stress_n10_qd": 8}
+# the GPU tracks, at least two per host core; about 5-15 s each on 16 cores)
+ORACLE_TRACK_SAMPLE = {"plain_n6_d": 64, "batched_n12_dd": 64, "learned_n16_d": 2048, "stress_n10_qd": 32}
 
 
 def oracle_track_rate(name, seed, limbs, h_min, sample):
@@ -439,8 +439,15 @@ def learned_vs_plain(ht, torch, world, name, m):
     train_s = time.perf_counter() - t0
     s = synth.config_system(name, case["eval_seed"])
     g = synth.random_gamma(case["eval_seed"])
-    # launch shape from the autotuner (plain rule, a sample of the paths); both arms use it
-    team, iters, _ = ht.ht_tune_track(ht.system_from(s, L), s.degrees(), g, case["tune_paths"], prm)
+    # launch shape from the autotuner (plain rule, a sample of the paths), kept
+    # in the tuning cache across runs on this machine; both arms use it
+    from paper_1505_00383_gb300 import tuning
+    cache = os.environ.get("HT_TUNE_CACHE", os.path.join(os.path.expanduser("~"), ".cache", "ht_tune_track.json"))
+    before = tuning._load(cache)
+    tuned = tuning.tuned_track_shape(ht.system_from(s, L), s, L, g, case["tune_paths"], prm, cache,
+                                     torch.cuda.get_device_name())
+    from_cache = tuning.cache_key(s, L, torch.cuda.get_device_name()) in before
+    team, iters = tuned.team_warps, tuned.iters_per_launch
     prm.team_warps, prm.iters_per_launch = team, iters
     out = {}
     for arm, nn in (("plain", None), ("learned", net)):
@@ -472,7 +479,7 @@ def learned_vs_plain(ht, torch, world, name, m):
            "counts": {"plain": counts(ra), "learned": counts(rb)},
            "counts_equal": counts(ra) == counts(rb), "endpoint_agreement_1e-10": agree,
            "launch_shape": {"team_warps": team, "iters_per_launch": iters,
-                            "tuned_on_paths": case["tune_paths"]},
+                            "tuned_on_paths": case["tune_paths"], "from_tuning_cache": from_cache},
            "train": {"systems": len(case["train_seeds"]), "paths_each": case["train_paths"], "precision": "D",
                      "epochs": case["epochs"],
                      "samples": int(sum(f.shape[0] for f in feats)), "first_loss": float(losses[0]),
@@ -742,9 +749,14 @@ def run_ours(a):
         cores = os.cpu_count() or 1
         budget = {1: 1024, 2: 64, 4: 16}
         v = cpu_oracle_rate(system, budget, threads=cores)
+        budget1 = {1: 128, 2: 8, 4: 2}
+        v1 = cpu_oracle_rate(system, budget1, threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                "sample": "%d D + %d DD + %d QD points of the sweep, all host cores" % (budget[1], budget[2],
-                                                                                         budget[4])}
+                                                                                         budget[4]),
+               "single_thread": {"value": v1, "unit": UNIT, "cores": 1,
+                                 "sample": "%d D + %d DD + %d QD points, one thread (the paper's one-core "
+                                           "comparison)" % (budget1[1], budget1[2], budget1[4])}}
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
