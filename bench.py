@@ -664,16 +664,19 @@ def run_ours(a):
         for L in PRECISIONS:  # warm-up (workspace allocation)
             ht.ht_eval_diff_host(sys_h[L], n, hx[L], hv[L], hj[L], stream)
         del vals, jacs
-        ts = []
+        ts, per_l = [], {L: [] for L in PRECISIONS}
         for s in range(max(1, min(a.steps, 3))):
             t0 = time.perf_counter()
             for L in PRECISIONS:
+                t1 = time.perf_counter()
                 ht.ht_eval_diff_host(sys_h[L], n, hx[L], hv[L], hj[L], stream)
+                per_l[L].append(time.perf_counter() - t1)
             ts.append(time.perf_counter() - t0)
         e2e_s = max_over_ranks(statistics.mean(ts), world, dev)
         e2e = {"value": world * n / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(sum(hx[L].numel() * 8 for L in PRECISIONS)),
-               "d2h_bytes_per_step": int(sum((hv[L].numel() + hj[L].numel()) * 8 for L in PRECISIONS))}
+               "d2h_bytes_per_step": int(sum((hv[L].numel() + hj[L].numel()) * 8 for L in PRECISIONS)),
+               "ms_per_precision": {NAMES[L]: [1e3 * v for v in per_l[L]] for L in PRECISIONS}}
 
     # roofline of the dominant kernel (the one with the largest share of the step)
     dom = max(PRECISIONS, key=lambda L: statistics.mean(launch_ms[L]))

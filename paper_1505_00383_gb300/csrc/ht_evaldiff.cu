@@ -109,12 +109,15 @@ __global__ void __launch_bounds__(128, 4) evaldiff_int_kernel(EvalArgs a, const 
 }
 
 // Block organisation of the same unit: a CTA takes a block of 32 points and
-// all polynomials, its warps dealing the polynomials round-robin.  The block's
+// a group of polynomials (as many as it has warps: one each).  The block's
 // converted points live once in shared memory (lane-interleaved, so every
 // access is a conflict-free 32-word row) instead of once per lane and unit
 // in local memory; the warp still walks one monomial with all lanes in step.
-// The sums are the same exact integers, so the results are those of the
-// per-unit kernel bit for bit.
+// Work items (polynomial group, point block) are ordered group-major, so a
+// CTA keeps one group's monomials and coefficients (a QD coefficient is 68
+// bytes) in its L1 across point blocks; the points are converted once per
+// item.  The sums are the same exact integers, so the results are those of
+// the per-unit kernel bit for bit.
 template <int L>
 __global__ void __launch_bounds__(256, 2) evaldiff_intblk_kernel(EvalArgs a, const mpi::fz<IntW<L>::W>* __restrict__ cfz,
                                                               const float* __restrict__ clg) {
@@ -125,9 +128,12 @@ __global__ void __launch_bounds__(256, 2) evaldiff_intblk_kernel(EvalArgs a, con
   Z P[64];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, T = blockDim.x >> 5;
   const int64_t n = a.v.npts, plane = (int64_t)a.nv * 2 * L * n, n_blocks = (n + 31) / 32;
+  const int n_groups = (a.np + T - 1) / T;
   const SmemPoints<L> X{xs, lane};
   const SmemLog lg{lgs, lane};
-  for (int64_t b = blockIdx.x; b < n_blocks; b += gridDim.x) {
+  for (int64_t item = blockIdx.x; item < n_blocks * n_groups; item += gridDim.x) {
+    const int64_t b = item % n_blocks;
+    const int g = (int)(item / n_blocks);
     const int64_t p = b * 32 + lane;
     const bool live = p < n;
     __syncthreads();  // the previous block's points are no longer read
@@ -143,7 +149,7 @@ __global__ void __launch_bounds__(256, 2) evaldiff_intblk_kernel(EvalArgs a, con
     }
     __syncthreads();
     if (!live) continue;  // lanes past the ragged tail sit the block out
-    for (int j = warp; j < a.np; j += T) {
+    for (int j = g * T + warp; j < a.np && j < (g + 1) * T; j += T) {
       double vre[L], vim[L];
       int_row<L>(a.v.mon_off, a.v.pairs, cfz, clg, a.poly_off[j], a.poly_off[j + 1], X, lg, a.nv,
                  a.jac + (int64_t)j * plane, n, p, vre, vim, P);
@@ -165,7 +171,7 @@ static int launch_int(const EvalArgs& a, const ht_system* s, int threads, cudaSt
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaldiff_intblk_kernel<L>, 256, smem);
     if (per_sm < 1) per_sm = 1;
-    int64_t want = (a.v.npts + 31) / 32;
+    int64_t want = (a.v.npts + 31) / 32 * ((a.np + 7) / 8);  // (point block, group of 8 polynomials) items
     int64_t grid = (int64_t)sm_count() * per_sm;
     if (grid > want) grid = want;
     evaldiff_intblk_kernel<L><<<(unsigned)grid, 256, smem, st>>>(a, cf, s->d_coef_lg);
