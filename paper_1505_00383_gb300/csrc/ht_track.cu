@@ -483,9 +483,11 @@ __device__ __forceinline__ cx<L> cx_from(const double* re, const double* im) {
 
 // INT: f and its Jacobian rows on the integer pipe (int_row: exact sums in
 // per-output fixed-point frames), the rest of the round in FP64 arithmetic.
-template <int L, bool LEARN, bool INT>
-__global__ void __launch_bounds__(256, L == 1 ? 3 : (L == 2 ? 2 : 1)) track_kernel(TrackArgs a) {
-  __shared__ double red[4][8][32];  // per-warp partials: residual, update, point norms; finiteness
+// MAXT: the largest team (8, or 16 for the wide instantiation that serves
+// few groups of double and double-double paths with more warps each).
+template <int L, bool LEARN, bool INT, int MAXT = 8>
+__global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 2 ? 2 : 1))) track_kernel(TrackArgs a) {
+  __shared__ double red[4][MAXT][32];  // per-warp partials: residual, update, point norms; finiteness
   __shared__ double sh_h[32];       // learned step of each lane's path
   __shared__ double sh_alpha[32];   // learned tangent correction of each lane's path
   __shared__ long long sh_slot[32]; // trace record slot of each lane's path (-1: none)
@@ -969,10 +971,14 @@ int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, 32 * team, dsm, st>>>(a);
   };
-  if (learn)
+  if (team > 8) {  // wide teams: plain step rule, double and double double (the host only asks for these)
+    if (learn || L == 4) return set_error(HT_EUNSUPPORTED, "track launch: teams above 8 warps need D or DD, plain rule");
+    in ? go(track_kernel<L, false, L == 2, 16>) : go(track_kernel<L, false, false, 16>);
+  } else if (learn) {
     in ? go(track_kernel<L, true, L != 1>) : go(track_kernel<L, true, false>);
-  else
+  } else {
     in ? go(track_kernel<L, false, L != 1>) : go(track_kernel<L, false, false>);
+  }
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HT_OK : cuda_fail(e, "track launch");
 }

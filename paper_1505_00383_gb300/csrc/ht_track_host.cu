@@ -264,7 +264,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
     ht_default_params(L, &P);
   if (!(P.h0 > 0) || !(P.h_min > 0) || !(P.h_max >= P.h_min) || !(P.f_up >= 1) || !(P.f_down > 0 && P.f_down < 1) ||
       P.newton_max < 1 || P.newton_max > 100 || P.polish_max < 0 || P.polish_max > 100 || P.max_steps < 1 ||
-      P.max_order < 0 || P.max_order > 7 || P.team_warps < 0 || P.team_warps > 8 || P.iters_per_launch < 0 ||
+      P.max_order < 0 || P.max_order > 7 || P.team_warps < 0 || P.team_warps > 16 || (P.team_warps > 8 && (L == 4 || (io && io->mlp))) || P.iters_per_launch < 0 ||
       P.rounds_per_sync < 0 || (P.rounds_per_sync & 1) || !(P.tol_dx > 0) || !(P.tol_res > 0) || !(P.tol_polish > 0) || !(P.r_div > 0) ||
       P.predictor < 0 || P.predictor > 2)
     return set_error(HT_EINVAL, "ht_track_paths: invalid parameters");
@@ -408,12 +408,21 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   // per-path workspace (A and R, 2 n (n + 1) complex entries per path) of the
   // resident groups stays in L2; on the n = 16 double workload 8 warps beat 1
   // warp by 1.7x and 4 warps by 4 %.
+  // While fewer groups are active than there are SMs (a small batch, or the
+  // tail of any run), a double or double-double group with more than 8 MGS
+  // columns gets 16 warps: every SM then runs at most one group, and the
+  // wider team shortens that group's round (fewer columns and polynomials per
+  // warp).  The learned step and QD (188+ registers a thread) keep 8.
+  const bool wide_ok = L <= 2 && !IO.mlp && n + 1 > 8;
   auto pick_team = [&](int64_t active) {
-    (void)active;
     if (P.team_warps > 0) return P.team_warps;
-    if (s->track_team > 0 && s->track_team <= 8) return s->track_team;
     int t = 1;
-    while (t < 8 && 2 * t <= n) t *= 2;
+    if (s->track_team > 0 && s->track_team <= 16) {
+      t = s->track_team;
+    } else {
+      while (t < 8 && 2 * t <= n) t *= 2;
+    }
+    if (t == 8 && wide_ok && (active + 31) / 32 < sm_count()) t = 16;
     return t;
   };
   int64_t active = m;
@@ -535,9 +544,10 @@ int ht_tune_track(ht_system* s, const int32_t* start_deg, const double* gamma, i
   const int saved_team = s->track_team, saved_iters = s->track_iters;
   double best = 1e300;
   int bt_team = 0, bt_iters = 0, rc = HT_OK;
-  const int teams[4] = {1, 2, 4, 8}, its[3] = {2, 4, 8};
-  for (int a = 0; a < 4 && rc == HT_OK; ++a) {
+  const int teams[5] = {1, 2, 4, 8, 16}, its[3] = {2, 4, 8};
+  for (int a = 0; a < 5 && rc == HT_OK; ++a) {
     if (teams[a] > 1 && teams[a] > n) continue;
+    if (teams[a] > 8 && (L == 4 || n + 1 <= 8)) continue;  // wide teams: D and DD with more than 8 columns
     for (int b = 0; b < 3 && rc == HT_OK; ++b) {
       ht_params Q = P;
       Q.team_warps = teams[a];

@@ -213,7 +213,7 @@ def test_team_size_does_not_change_integer_evaluation_results(ht, L):
     s = synth.config_system("stress_n10_qd" if L == 4 else "batched_n12_dd")
     gam = synth.random_gamma(1)
     base = track_gpu(ht, s, L, 96, gamma=gam, team_warps=1, iters_per_launch=2, rounds_per_sync=2)
-    for tw in (2, 8):
+    for tw in (2, 8) + ((16,) if L == 2 else ()):  # 16 warps: the wide instantiation (D and DD)
         r = track_gpu(ht, s, L, 96, gamma=gam, team_warps=tw)
         for k in ("x_end", "status", "t_end", "steps"):
             assert np.array_equal(r[k], base[k], equal_nan=True), (tw, k)
@@ -577,3 +577,20 @@ def test_hermite_results_do_not_depend_on_the_launch_shape(ht, L):
         r = track_gpu(ht, s, L, 96 if L == 4 else 64, gamma=gam, team_warps=tw, predictor=2)
         for k in ("x_end", "status", "t_end", "steps"):
             assert np.array_equal(r[k], base[k], equal_nan=True), (tw, k)
+
+
+def test_wide_teams_give_the_same_bits_in_double(ht):
+    """16-warp teams (the wide instantiation the tracker picks while fewer
+    groups than SMs are active) against one-warp teams on the n = 16 double
+    workload; QD and the learned step refuse them."""
+    s = synth.config_system("learned_n16_d")
+    gam = synth.random_gamma(3)
+    base = track_gpu(ht, s, 1, 64, gamma=gam, team_warps=1, iters_per_launch=3, rounds_per_sync=2)
+    for tw in (16, 0):  # 0: the automatic choice, 16 here (2 groups)
+        r = track_gpu(ht, s, 1, 64, gamma=gam, team_warps=tw)
+        for k in ("x_end", "status", "t_end", "steps"):
+            assert np.array_equal(r[k], base[k], equal_nan=True), (tw, k)
+    q = synth.config_system("stress_n10_qd")
+    with pytest.raises(ht.HTError) as e:
+        track_gpu(ht, q, 4, 32, team_warps=16)
+    assert e.value.code == ht.HT_EINVAL
