@@ -286,6 +286,19 @@ __device__ __forceinline__ rl<L> acc_abs2(rl<L> s, const cx<L>& v) {
   }
 }
 
+// The warp that handles column j in the phase that projects on q_q: the
+// pivot column q + 1 (which its warp also normalises) goes to warp
+// wp = (q + 1) % T; with 4 or more warps the other columns go round-robin to
+// the other T - 1 warps, so the pivot's normalisation is not stacked on a
+// second projection; with fewer warps they go round-robin to all, starting
+// after wp.
+__device__ __forceinline__ int mgs_col_warp(int j, int q, int T) {
+  const int wp = (q + 1) % T;
+  if (j == q + 1) return wp;
+  const int k = j - q - 2;  // index among the other columns
+  return T >= 4 ? (wp + 1 + k % (T - 1)) % T : (wp + 1 + k) % T;
+}
+
 template <int L>
 __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
                          int warp, int T, int nrhs = 1, double* x2 = nullptr) {
@@ -309,13 +322,13 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
   }
   __syncthreads();
   // Look-ahead: in the phase that projects the later columns on q_q, the
-  // owner of column q + 1 projects it first and normalises it at once, while
-  // the other warps project their columns; one barrier per column.  Every
-  // column sees the same operations in the same order as without look-ahead.
+  // warp of column q + 1 projects it and normalises it at once, while the
+  // other warps project the other columns (mgs_col_warp); one barrier per
+  // column.  Every column sees the same operations in the same order as
+  // without look-ahead.
   for (int q = 0; q < cols; ++q) {
-    int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
-    for (int j = j0; j < W; j += T) {
-      if (!act) continue;
+    for (int j = q + 1; j < W; ++j) {
+      if (!act || mgs_col_warp(j, q, T) != warp) continue;
       cx<L> r = czero<L>();
       for (int i = 0; i < rows; ++i)
         r = acc_conj_mul<L>(r, ld<L>(A, (int64_t)i * W + q, m, p), ld<L>(A, (int64_t)i * W + j, m, p));
@@ -392,13 +405,16 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
     normalise(0, Q);
   }
   __syncthreads();
-  // Look-ahead as in mgs_team: the owner of column q + 1 projects it first
-  // and normalises it from the registers at once; one barrier per column.
+  // Look-ahead as in mgs_team: the warp of column q + 1 projects it and
+  // normalises it at once, the other columns go to the other warps; one
+  // barrier per column.
   for (int q = 0; q < cols; ++q) {
-    const int j0 = q + 1 + ((warp - (q + 1) % T) + T) % T;  // first column > q owned by this warp
-    if (act && j0 < Wc) {
+    bool any = false;  // this warp has a column in this phase
+    for (int j = q + 1; j < Wc; ++j) any = any || mgs_col_warp(j, q, T) == warp;
+    if (act && any) {
       for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc + q, m, p);
-      for (int j = j0; j < Wc; j += T) {
+      for (int j = q + 1; j < Wc; ++j) {
+        if (mgs_col_warp(j, q, T) != warp) continue;
         for (int i = 0; i < rows; ++i) col[i] = ldz<L>(A, (int64_t)i * Wc + j, m, p);
         const Z r = mpi::dot_conj<W, N>(Q, col, rows, S);
         stz<L>(R, (int64_t)q * Wc + j, m, p, r);
