@@ -167,7 +167,15 @@ static int launch_int(const EvalArgs& a, const ht_system* s, int threads, cudaSt
   const auto* cf = reinterpret_cast<const mpi::fz<IntW<L>::W>*>(s->d_coef_fz);
   if (threads == 256) {  // block organisation (points in shared memory)
     const size_t smem = (size_t)a.nv * 32 * ((2 * IntW<L>::W + 1) * sizeof(int32_t) + sizeof(float));
-    cudaFuncSetAttribute(evaldiff_intblk_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // raise the kernel's dynamic shared-memory limit (per device) only when a
+    // larger system needs more, not on every launch
+    static size_t smem_set[64] = {0};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64 || smem > smem_set[dev]) {
+      cudaFuncSetAttribute(evaldiff_intblk_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (dev >= 0 && dev < 64) smem_set[dev] = smem;
+    }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, evaldiff_intblk_kernel<L>, 256, smem);
     if (per_sm < 1) per_sm = 1;
