@@ -181,6 +181,32 @@ def _traffic(L):
     return float(m.group(1)) if m else None
 
 
+def _track_sha():
+    h = hashlib.sha256()
+    for f in ("ht_track.cu", "ht_track.h", "ht_eval.cuh", "ht_int_row.cuh", "ht_mp.cuh", "ht_mpi.cuh", "ht_mpi_eval.cuh",
+              "ht_mpi_ops.cuh", "ht_mlp.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_1505_00383_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def _track_pipes():
+    """Pipe utilisation of the QD tracker kernel from the committed ncu
+    summary, if the tracker sources are unchanged since it was taken."""
+    path = os.path.join(ROOT, "profiles", "track_qd_n10_59049paths.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"track_sources_sha256:\s*([0-9a-f]+)", txt)
+    if not m or m.group(1) != _track_sha():
+        return None
+    out = {"source": "profiles/track_qd_n10_59049paths.md (ncu, one launch at 16,384 paths)"}
+    for key in ("fp64_pipe_pct", "alu_pipe_pct", "fma_pipe_pct", "issue_active_pct", "warps_active_pct"):
+        m = re.search(r"%s:\s*([0-9.]+)" % key, txt)
+        if m:
+            out[key] = float(m.group(1))
+    return out
+
+
 def _kernel_sha():
     h = hashlib.sha256()
     for f in ("ht_evaldiff.cu", "ht_eval.cuh", "ht_int_row.cuh", "ht_mp.cuh", "ht_mpi.cuh", "ht_mpi_eval.cuh"):
@@ -743,6 +769,8 @@ def run_ours(a):
                          ("stress_n10_qd", a.stress, "stress_n10_qd_vs_plain")):
         if m > 0:
             tracking[key] = learned_vs_plain(ht, torch, world, name, m)
+            if name == "stress_n10_qd":
+                tracking[key]["pipes"] = _track_pipes()
             if oracle_side:
                 tracking[key]["cpu_baseline"] = oracle_track_rate(name, LEARNED_CASES[name]["eval_seed"],
                                                                   TRACK_LIMBS[name], 1e-9, ORACLE_TRACK_SAMPLE[name])
