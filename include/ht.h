@@ -260,10 +260,9 @@ typedef struct ht_params {
   int32_t polish_max; /* Newton steps at t = 1 (0..100) */
   int32_t max_steps;  /* steps (accepted + rejected) before a path fails */
   int32_t max_order;  /* predictor order: extrapolation through up to max_order + 1 points (0..7) */
-  int32_t team_warps;       /* warps serving one group of 32 paths (1..8; 16 for D and DD with the
-                               plain rule); 0 = chosen per round: the tuned or built-in size, and 16
-                               warps for D and DD systems with n >= 8 while fewer groups than SMs
-                               are active */
+  int32_t team_warps;       /* warps serving one group of 32 paths (1..8; 16 for D and DD);
+                               0 = chosen per round: the tuned or built-in size, and 16 warps for D
+                               and DD systems with n >= 8 while fewer groups than SMs are active */
   int32_t iters_per_launch; /* Newton steps per kernel launch; 0 = default (4) */
   int32_t rounds_per_sync;  /* launches between host reads of the active count, even; 0 = default (8) */
   int32_t predictor;        /* 0 extrapolation through up to max_order + 1 accepted points (default);

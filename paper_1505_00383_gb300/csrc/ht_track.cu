@@ -500,7 +500,8 @@ __device__ __forceinline__ cx<L> cx_from(const double* re, const double* im) {
 // INT: f and its Jacobian rows on the integer pipe (int_row: exact sums in
 // per-output fixed-point frames), the rest of the round in FP64 arithmetic.
 // MAXT: the largest team (8, or 16 for the wide instantiation that serves
-// few groups of double and double-double paths with more warps each).
+// few groups of double and double-double paths with more warps each, and
+// any group when the autotuner picks 16).
 template <int L, bool LEARN, bool INT, int MAXT = 8>
 __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 2 ? 2 : 1))) track_kernel(TrackArgs a) {
   __shared__ double red[4][MAXT][32];  // per-warp partials: residual, update, point norms; finiteness
@@ -987,9 +988,12 @@ int launch_track_l(const TrackArgs& a, int team, int64_t max_groups, cudaStream_
     if (grid < 1) grid = 1;
     kern<<<(unsigned)grid, 32 * team, dsm, st>>>(a);
   };
-  if (team > 8) {  // wide teams: plain step rule, double and double double (the host only asks for these)
-    if (learn || L == 4) return set_error(HT_EUNSUPPORTED, "track launch: teams above 8 warps need D or DD, plain rule");
-    in ? go(track_kernel<L, false, L == 2, 16>) : go(track_kernel<L, false, false, 16>);
+  if (team > 8) {  // wide teams: double and double double (the host only asks for these)
+    if (L == 4) return set_error(HT_EUNSUPPORTED, "track launch: teams above 8 warps need D or DD");
+    if (learn)
+      in ? go(track_kernel<L, true, L == 2, 16>) : go(track_kernel<L, true, false, 16>);
+    else
+      in ? go(track_kernel<L, false, L == 2, 16>) : go(track_kernel<L, false, false, 16>);
   } else if (learn) {
     in ? go(track_kernel<L, true, L != 1>) : go(track_kernel<L, true, false>);
   } else {

@@ -264,7 +264,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
     ht_default_params(L, &P);
   if (!(P.h0 > 0) || !(P.h_min > 0) || !(P.h_max >= P.h_min) || !(P.f_up >= 1) || !(P.f_down > 0 && P.f_down < 1) ||
       P.newton_max < 1 || P.newton_max > 100 || P.polish_max < 0 || P.polish_max > 100 || P.max_steps < 1 ||
-      P.max_order < 0 || P.max_order > 7 || P.team_warps < 0 || P.team_warps > 16 || (P.team_warps > 8 && (L == 4 || (io && io->mlp))) || P.iters_per_launch < 0 ||
+      P.max_order < 0 || P.max_order > 7 || P.team_warps < 0 || P.team_warps > 16 || (P.team_warps > 8 && L == 4) || P.iters_per_launch < 0 ||
       P.rounds_per_sync < 0 || (P.rounds_per_sync & 1) || !(P.tol_dx > 0) || !(P.tol_res > 0) || !(P.tol_polish > 0) || !(P.r_div > 0) ||
       P.predictor < 0 || P.predictor > 2)
     return set_error(HT_EINVAL, "ht_track_paths: invalid parameters");
@@ -412,8 +412,8 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   // tail of any run), a double or double-double group with more than 8 MGS
   // columns gets 16 warps: every SM then runs at most one group, and the
   // wider team shortens that group's round (fewer columns and polynomials per
-  // warp).  The learned step and QD (188+ registers a thread) keep 8.
-  const bool wide_ok = L <= 2 && !IO.mlp && n + 1 > 8;
+  // warp).  QD (200+ registers a thread) keeps 8.
+  const bool wide_ok = L <= 2 && n + 1 > 8;
   auto pick_team = [&](int64_t active) {
     if (P.team_warps > 0) return P.team_warps;
     int t = 1;

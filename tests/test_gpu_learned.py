@@ -362,3 +362,19 @@ def test_trained_network_gains_over_the_plain_rule(ht):
         tot_plain += a["stats"]["newton"]
         tot_learn += b["stats"]["newton"]
     assert tot_learn < 0.95 * tot_plain, (tot_learn, tot_plain)
+
+
+def test_learned_step_with_wide_teams_gives_the_same_bits(ht):
+    """The learned step in the 16-warp instantiation (which the tracker takes
+    while fewer groups than SMs are active, and the autotuner may choose)
+    tracks exactly as with 8 warps."""
+    from paper_1505_00383_gb300 import learned
+    s = synth.config_system("learned_n16_d")
+    gam = synth.random_gamma(5)
+    net = _net(ht, learned.init_params(9))
+    out = {}
+    for tw in (8, 16):
+        prm = ht.ht_default_params(1, h_min=1e-9, team_warps=tw)
+        out[tw] = learned.track(s, 1, gam, 96, prm, net=net)
+    assert np.array_equal(out[8]["x_end"], out[16]["x_end"]) and np.array_equal(out[8]["status"], out[16]["status"])
+    assert out[8]["stats"]["newton"] == out[16]["stats"]["newton"]

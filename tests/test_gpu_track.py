@@ -582,7 +582,7 @@ def test_hermite_results_do_not_depend_on_the_launch_shape(ht, L):
 def test_wide_teams_give_the_same_bits_in_double(ht):
     """16-warp teams (the wide instantiation the tracker picks while fewer
     groups than SMs are active) against one-warp teams on the n = 16 double
-    workload; QD and the learned step refuse them."""
+    workload; QD refuses them."""
     s = synth.config_system("learned_n16_d")
     gam = synth.random_gamma(3)
     base = track_gpu(ht, s, 1, 64, gamma=gam, team_warps=1, iters_per_launch=3, rounds_per_sync=2)
