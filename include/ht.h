@@ -164,9 +164,10 @@ int ht_eval_diff_unfused(ht_system* sys, int64_t n_pts, const double* x, double*
  *   threads  CTA size 64, 128 or 256, or 0 for the default (128); for
  *            variant 2, 128 (or 0, 64) runs one unit of 32 points and one
  *            polynomial per warp with the lane's point in local memory, and
- *            256 runs work items of 32 points and 8 polynomials per CTA (one
- *            polynomial per warp) with the points in shared memory (the same
- *            bits either way)
+ *            256 runs work items of 32 points and a group of polynomials per
+ *            CTA (one polynomial per warp: 16-warp CTAs for systems of at
+ *            least 16 polynomials, else 8) with the points in shared memory
+ *            (the same bits either way)
  * Variants 0, 1 and 3 perform the same operations in the same order, so their
  * results are bitwise identical; variant 2 meets the same accuracy bound
  * (a small multiple of 2^(-53 L) times the sum of the moduli of the terms of

@@ -5,6 +5,7 @@
 // evaluation kernel and the tracker both call it.
 #pragma once
 #include "ht_mpi_eval.cuh"
+#include "ht_mpi_ops.cuh"
 
 namespace ht {
 
@@ -36,17 +37,90 @@ __device__ __forceinline__ void st_fix(double* jrow, int64_t i, int64_t n, int64
   }
 }
 
-// The Jacobian row accumulates in place in the output slots.
+// The Jacobian row accumulates in place in the output slots: in the doubles
+// of the vertical layout (2L doubles hold the 2 x 2L int32 limbs) ...
 template <int L>
 struct RowAcc {
   double* jrow;
   int64_t n, p;
+  static constexpr int WA = IntW<L>::WA;
+  __device__ __forceinline__ void zero(int v) {
+    int32_t z[WA];
+#pragma unroll
+    for (int k = 0; k < WA; ++k) z[k] = 0;
+    st_fix<L>(jrow, v, n, p, z, z);
+  }
   __device__ __forceinline__ void add(int v, const mpi::fz<IntW<L>::W>& d, int e, int F) {
-    constexpr int WA = IntW<L>::WA;
     int32_t ar[WA], ai[WA];
     ld_fix<L>(jrow, v, n, p, ar, ai);
     mpi::acc_add_fast<IntW<L>::W, WA>(ar, ai, d, e, F);
     st_fix<L>(jrow, v, n, p, ar, ai);
+  }
+  // entry v as L doubles per component, times scale (rounded once)
+  __device__ __forceinline__ void finish(int v, int F, double scale) {
+    int32_t ar[WA], ai[WA];
+    ld_fix<L>(jrow, v, n, p, ar, ai);
+    double o[L];
+    if (scale == 1.0)
+      mpi::fixed_to_doubles<WA, L>(ar, F, o);
+    else
+      mpi::fixed_scaled_to_doubles<WA, L>(ar, F, scale, o);
+#pragma unroll
+    for (int l = 0; l < L; ++l) jrow[((int64_t)(v * 2) * L + l) * n + p] = o[l];
+    if (scale == 1.0)
+      mpi::fixed_to_doubles<WA, L>(ai, F, o);
+    else
+      mpi::fixed_scaled_to_doubles<WA, L>(ai, F, scale, o);
+#pragma unroll
+    for (int l = 0; l < L; ++l) jrow[((int64_t)(v * 2 + 1) * L + l) * n + p] = o[l];
+  }
+};
+
+// ... or in limb-string slots ([entry][2W+1][n] int32 words: exponent, re
+// limbs, im limbs; the accumulators use the limb words), finished as limb
+// strings for the integer least squares.
+template <int L>
+struct RowAccFz {
+  int32_t* zrow;
+  int64_t n, p;
+  static constexpr int W = IntW<L>::W, WA = IntW<L>::WA;
+  static_assert(WA <= W, "the accumulator limbs must fit the limb words");
+  __device__ __forceinline__ int32_t* at(int v) const { return zrow + (int64_t)v * (2 * W + 1) * n + p; }
+  __device__ __forceinline__ void zero(int v) {
+    int32_t* q = at(v);
+#pragma unroll
+    for (int k = 0; k < WA; ++k) q[(1 + k) * n] = q[(1 + W + k) * n] = 0;
+  }
+  __device__ __forceinline__ void add(int v, const mpi::fz<W>& d, int e, int F) {
+    int32_t* q = at(v);
+    int32_t ar[WA], ai[WA];
+#pragma unroll
+    for (int k = 0; k < WA; ++k) {
+      ar[k] = q[(1 + k) * n];
+      ai[k] = q[(1 + W + k) * n];
+    }
+    mpi::acc_add_fast<W, WA>(ar, ai, d, e, F);
+#pragma unroll
+    for (int k = 0; k < WA; ++k) {
+      q[(1 + k) * n] = ar[k];
+      q[(1 + W + k) * n] = ai[k];
+    }
+  }
+  __device__ __forceinline__ void finish(int v, int F, double scale) {
+    int32_t* q = at(v);
+    int32_t ar[WA], ai[WA];
+#pragma unroll
+    for (int k = 0; k < WA; ++k) {
+      ar[k] = q[(1 + k) * n];
+      ai[k] = q[(1 + W + k) * n];
+    }
+    const mpi::fz<W> z = mpi::fixed_scaled_to_fz<WA, W>(ar, ai, F, scale);
+    q[0] = z.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      q[(1 + k) * n] = z.r[k];
+      q[(1 + W + k) * n] = z.i[k];
+    }
   }
 };
 
@@ -68,37 +142,43 @@ __device__ __forceinline__ void int_point(const double* __restrict__ x, int nv, 
 }
 
 // Monomials m0..m1 of one polynomial at the lane's point: the value as L
-// doubles per component (vre, vim) and the gradient written as doubles into
-// jrow ([nv][2][L][n], entry i at point p).  X and lg are indexable by
-// variable (local arrays or shared-memory views); P is scratch for the
-// forward products (max monomial size entries).
-template <int L, class XA, class LG>
-__device__ void int_row(const int32_t* __restrict__ mon_off, const uint16_t* __restrict__ pairs,
-                        const mpi::fz<IntW<L>::W>* __restrict__ cfz, const float* __restrict__ clg, int m0, int m1,
-                        const XA& X, const LG& lg, int nv, double* jrow, int64_t n, int64_t p, double* vre,
-                        double* vim, mpi::fz<IntW<L>::W>* P) {
+// doubles per component (vre, vim) and the gradient times scale in the row
+// storage (RowAcc: doubles in jrow's layout [nv][2][L][n]; RowAccFz: limb
+// strings), each entry rounded once from its exact fixed-point product.  X
+// and lg are indexable by variable (local arrays or shared-memory views); P
+// is scratch for the forward products (max monomial size entries).
+template <int L, class XA, class LG, class PS, class Row>
+__device__ void int_row_in(const int32_t* __restrict__ mon_off, const uint16_t* __restrict__ pairs,
+                           const mpi::fz<IntW<L>::W>* __restrict__ cfz, const float* __restrict__ clg, int m0,
+                           int m1, const XA& X, const LG& lg, int nv, Row& row, double* vre, double* vim, PS* P,
+                           double scale) {
   constexpr int WA = IntW<L>::WA;
   int Fv[kIntMaxVars];
   const int F = mpi::frames_for_poly<WA>(mon_off, pairs, clg, m0, m1, lg, nv, Fv);
   int32_t vr[WA], vi[WA];
 #pragma unroll
   for (int k = 0; k < WA; ++k) vr[k] = vi[k] = 0;
-  for (int i = 0; i < nv; ++i) st_fix<L>(jrow, i, n, p, vr, vi);
-  RowAcc<L> acc{jrow, n, p};
-  mpi::eval_poly_int<L>(mon_off, pairs, cfz, m0, m1, X, F, Fv, acc, vr, vi, P);
+  for (int i = 0; i < nv; ++i) row.zero(i);
+  mpi::eval_poly_int<L>(mon_off, pairs, cfz, m0, m1, X, F, Fv, row, vr, vi, P);
   mpi::fixed_to_doubles<WA, L>(vr, F, vre);
   mpi::fixed_to_doubles<WA, L>(vi, F, vim);
-  double o[L];
-  for (int i = 0; i < nv; ++i) {
-    int32_t ar[WA], ai[WA];
-    ld_fix<L>(jrow, i, n, p, ar, ai);
-    mpi::fixed_to_doubles<WA, L>(ar, Fv[i], o);
-#pragma unroll
-    for (int l = 0; l < L; ++l) jrow[((int64_t)(i * 2) * L + l) * n + p] = o[l];
-    mpi::fixed_to_doubles<WA, L>(ai, Fv[i], o);
-#pragma unroll
-    for (int l = 0; l < L; ++l) jrow[((int64_t)(i * 2 + 1) * L + l) * n + p] = o[l];
-  }
+  for (int i = 0; i < nv; ++i) row.finish(i, Fv[i], scale);
+}
+template <int L, class XA, class LG, class PS>
+__device__ void int_row(const int32_t* __restrict__ mon_off, const uint16_t* __restrict__ pairs,
+                        const mpi::fz<IntW<L>::W>* __restrict__ cfz, const float* __restrict__ clg, int m0, int m1,
+                        const XA& X, const LG& lg, int nv, double* jrow, int64_t n, int64_t p, double* vre,
+                        double* vim, PS* P, double scale = 1.0) {
+  RowAcc<L> row{jrow, n, p};
+  int_row_in<L>(mon_off, pairs, cfz, clg, m0, m1, X, lg, nv, row, vre, vim, P, scale);
+}
+template <int L, class XA, class LG, class PS>
+__device__ void int_row_fz(const int32_t* __restrict__ mon_off, const uint16_t* __restrict__ pairs,
+                           const mpi::fz<IntW<L>::W>* __restrict__ cfz, const float* __restrict__ clg, int m0,
+                           int m1, const XA& X, const LG& lg, int nv, int32_t* zrow, int64_t n, int64_t p,
+                           double* vre, double* vim, PS* P, double scale) {
+  RowAccFz<L> row{zrow, n, p};
+  int_row_in<L>(mon_off, pairs, cfz, clg, m0, m1, X, lg, nv, row, vre, vim, P, scale);
 }
 
 // Views of a CTA's converted points in shared memory, lane-interleaved so a

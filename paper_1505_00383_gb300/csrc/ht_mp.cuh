@@ -385,6 +385,21 @@ __device__ __forceinline__ rl<L> r_diff(double a, double b) {
     }
   }
 }
+// Limb l of an L-limb real, and an L-limb real from its limbs (for staging
+// values in shared memory).
+__device__ __forceinline__ double r_limb(double a, int) { return a; }
+__device__ __forceinline__ double r_limb(dd a, int l) { return l == 0 ? a.hi : a.lo; }
+__device__ __forceinline__ double r_limb(qd a, int l) { return a.x[l]; }
+template <int L>
+__device__ __forceinline__ rl<L> r_of(const double* v) {
+  if constexpr (L == 1) {
+    return v[0];
+  } else if constexpr (L == 2) {
+    return dd{v[0], v[1]};
+  } else {
+    return qd{{v[0], v[1], v[2], v[3]}};
+  }
+}
 __device__ __forceinline__ bool r_finite(double a) { return isfinite(a); }
 __device__ __forceinline__ bool r_finite(dd a) { return isfinite(a.hi) && isfinite(a.lo); }
 __device__ __forceinline__ bool r_finite(qd a) {

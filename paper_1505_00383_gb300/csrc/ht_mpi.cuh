@@ -43,6 +43,35 @@ struct fz {
   int32_t r[W], i[W];
 };
 
+// fz<W> padded to a multiple of 16 bytes and aligned to 16, for scratch kept in
+// local memory (the forward products of the sweep): it moves in 128-bit words.
+template <int W>
+struct alignas(16) fzs {
+  static constexpr int NW = (2 * W + 1 + 3) / 4 * 4;
+  int32_t w[NW];
+  HT_HD fzs() {}
+  HT_HD fzs(const fz<W>& z) {
+    w[0] = z.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      w[1 + k] = z.r[k];
+      w[1 + W + k] = z.i[k];
+    }
+#pragma unroll
+    for (int k = 2 * W + 1; k < NW; ++k) w[k] = 0;
+  }
+  HT_HD operator fz<W>() const {
+    fz<W> z;
+    z.f = w[0];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      z.r[k] = w[1 + k];
+      z.i[k] = w[1 + W + k];
+    }
+    return z;
+  }
+};
+
 // Bit length of v (0 for 0): one count-leading-zeros instruction.
 HT_HD int bitlen32(uint32_t v) {
 #if defined(__CUDA_ARCH__)
@@ -291,59 +320,80 @@ HT_HD bool acc_add(int32_t* acc_r, int32_t* acc_i, const fz<W>& z, int e, int F)
   return true;
 }
 
-// One component of e * z added into fixed-point column sums acc[WA] (limb 0
-// weight 2^F), by one shift of the whole two's complement limb string: limb k
-// of z sits at bit 29 k + (f - F) of the accumulator frame.  Bits that land
-// below limb 0 are dropped (truncation: at most one unit of the last limb).
-// -28 <= f - F required above the frame's top (the caller's bound).
+// One component of z as WA digits of a fixed-point frame, by one shift of the
+// whole two's complement limb string: limb k of z sits at bit 29 k + (f - F)
+// of the frame, F - f = 29 (q - 1) + r with 0 <= q <= W.  Bits that land
+// below limb 0 are dropped (truncation: at most one unit of the last limb);
+// digits 0..WA-2 come out in [0, 2^29), the top one signed.  With one zero
+// digit prepended below limb 0, digit j is bits [r, r + 29) of string digits
+// j + q and j + q + 1; the string is shifted down by q one bit of q at a time
+// (static indices only).
 template <int W, int WA>
-HT_HD void add_shifted_comp(int64_t* acc, const int32_t* z, int s, int e) {
-  // s = F - f: right shift in bits (may be slightly negative: left shift)
-  int32_t D[W + WA + 3];
-  const int32_t ext = z[W - 1] < 0 ? MASK : 0;
+HT_HD void shifted_digits(const int32_t* z, int q, int r, int32_t* v) {
+  constexpr int N = W + WA + 4;
+  constexpr int TOP = W >= 8 ? 8 : (W >= 4 ? 4 : (W >= 2 ? 2 : 1));  // highest bit of q <= W
+  const int32_t ext = z[W - 1] < 0 ? MASK : 0;  // the string's sign digits
+  int32_t D[N];
+  D[0] = 0;
 #pragma unroll
-  for (int k = 0; k < W - 1; ++k) D[k] = z[k];
-  D[W - 1] = z[W - 1] & MASK;
+  for (int k = 0; k < W - 1; ++k) D[1 + k] = z[k];
+  D[W] = z[W - 1] & MASK;
 #pragma unroll
-  for (int k = W; k < W + WA + 3; ++k) D[k] = ext;
-  if (s >= 0) {
-    const int q = s / RB, r = s % RB;
-    if (q >= W) {
-      return;  // below the accumulator's last limb
-    }
+  for (int k = W + 1; k < N; ++k) D[k] = ext;
 #pragma unroll
-    for (int j = 0; j < WA; ++j) {
-      const int32_t lo = D[j + q], hi = D[j + q + 1];
-      int32_t v = r == 0 ? lo : (int32_t)((((uint32_t)lo >> r) | ((uint32_t)hi << (RB - r))) & (uint32_t)MASK);
-      if (j == WA - 1) v = (v << (32 - RB)) >> (32 - RB);  // the top limb carries the sign
-      acc[j] += (int64_t)e * v;
-    }
-  } else {
-    const int u = -s;  // 1..28
+  for (int b = TOP; b >= 1; b >>= 1) {
+    const bool take = (q & b) != 0;
 #pragma unroll
-    for (int j = 0; j < WA; ++j) {
-      const int32_t lo = j > 0 ? D[j - 1] : 0, hi = D[j];
-      int32_t v = (int32_t)((((uint32_t)hi << u) | ((uint32_t)lo >> (RB - u))) & (uint32_t)MASK);
-      if (j == WA - 1) v = (v << (32 - RB)) >> (32 - RB);
-      acc[j] += (int64_t)e * v;
-    }
+    for (int k = 0; k < N; ++k) D[k] = take ? (k + b < N ? D[k + b] : ext) : D[k];
+  }
+#pragma unroll
+  for (int j = 0; j < WA; ++j) {
+    v[j] = (int32_t)((((uint32_t)D[j] >> r) | ((uint32_t)D[j + 1] << (RB - r))) & (uint32_t)MASK);
+    if (j == WA - 1) v[j] = (v[j] << (32 - RB)) >> (32 - RB);  // the top digit carries the sign
+  }
+}
+
+// Carry-propagate int32 limbs (limbs 0..N-2 to [0, 2^29), the top signed).
+template <int N>
+HT_HD void carry32(int32_t* a) {
+#pragma unroll
+  for (int j = 0; j + 1 < N; ++j) {
+    const int32_t c = a[j] >> RB;  // floor division (arithmetic shift)
+    a[j] &= MASK;
+    a[j + 1] += c;
   }
 }
 
 // e * z into int32 accumulators acc_r, acc_i [WA] (frame F), carried.
 // Returns false (adding nothing) if z's frame lies more than 28 bits above F.
+// For |e| <= 3 the sums stay in 32 bits: a limb below the top holds at most
+// 2^29 - 1, takes e d with |e d| <= 3 (2^29 - 1) and a carry of at most 3 in
+// magnitude, so it stays inside int32 before its own carry.
 template <int W, int WA>
 HT_HD bool acc_add_fast(int32_t* acc_r, int32_t* acc_i, const fz<W>& z, int e, int F) {
   const int s = F - z.f;
   if (s < -(RB - 1)) return false;
+  const int sp = s + RB, q = sp / RB, r = sp % RB;
+  if (q > W) return true;  // below the accumulator's last limb
+  int32_t dr[WA], di[WA];
+  shifted_digits<W, WA>(z.r, q, r, dr);
+  shifted_digits<W, WA>(z.i, q, r, di);
+  if (e >= -3 && e <= 3) {
+#pragma unroll
+    for (int k = 0; k < WA; ++k) {
+      acc_r[k] += e * dr[k];
+      acc_i[k] += e * di[k];
+    }
+    carry32<WA>(acc_r);
+    carry32<WA>(acc_i);
+    return true;
+  }
   int64_t ar[WA], ai[WA];
 #pragma unroll
   for (int k = 0; k < WA; ++k) {
-    ar[k] = acc_r[k];
-    ai[k] = acc_i[k];
+    ar[k] = acc_r[k] + (int64_t)e * dr[k];
+    ai[k] = acc_i[k] + (int64_t)e * di[k];
   }
-  add_shifted_comp<W, WA>(ar, z.r, s, e);
-  add_shifted_comp<W, WA>(ai, z.i, s, e);
   carry<WA>(ar);
   carry<WA>(ai);
 #pragma unroll
@@ -413,6 +463,37 @@ HT_HD void fixed_to_doubles(const int32_t* a, int F, double* out) {
     hi_bit = lo_bit - 1;
     if (hi_bit < 0) break;
   }
+}
+
+// s a for a fixed-point value a (WA limbs, frame F) and a double s, to L
+// doubles: the product is formed exactly in WA + 2 limbs (s's significand in
+// a 24-bit and a 29-bit part) and converted once, as fixed_to_doubles does.
+// For s = 1 the doubles are those of fixed_to_doubles.
+template <int WA, int L>
+HT_HD void fixed_scaled_to_doubles(const int32_t* a, int F, double s, double* out) {
+  int64_t ms;
+  int es;
+  decompose(s, ms, es);  // s = ms 2^es, |ms| < 2^53
+  const bool neg = ms < 0;
+  const uint64_t u = (uint64_t)(neg ? -ms : ms);
+  const int64_t lo = (int64_t)(u & (uint64_t)MASK), hi = (int64_t)(u >> RB);
+  int64_t c[WA + 2];
+#pragma unroll
+  for (int k = 0; k < WA + 2; ++k) c[k] = 0;
+#pragma unroll
+  for (int k = 0; k < WA; ++k) {  // |a_k lo| < 2^58, |a_k hi| < 2^53
+    c[k] += (int64_t)a[k] * lo;
+    c[k + 1] += (int64_t)a[k] * hi;
+  }
+  if (neg) {
+#pragma unroll
+    for (int k = 0; k < WA + 2; ++k) c[k] = -c[k];
+  }
+  carry<WA + 2>(c);
+  int32_t b[WA + 2];  // the top limb holds |a| |ms| / 2^(29 (WA + 1)) < 2^24
+#pragma unroll
+  for (int k = 0; k < WA + 2; ++k) b[k] = (int32_t)c[k];
+  fixed_to_doubles<WA + 2, L>(b, F + es, out);
 }
 
 }  // namespace mpi

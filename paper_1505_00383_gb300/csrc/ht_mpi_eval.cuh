@@ -89,9 +89,9 @@ HT_HD int frames_for_poly(const int32_t* mon_off, const uint16_t* pairs, const f
 // and a single accumulation site, so the multi-limb product is emitted once
 // (the 8-limb product is several hundred instructions) and its operands stay
 // in registers.
-template <int L, class XA, class Acc, class ValAdd>
+template <int L, class XA, class Acc, class ValAdd, class PS>
 HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m,
-                          const XA& X, const int* Fv, Acc& acc, ValAdd& val_add, fz<IntW<L>::W>* P) {
+                          const XA& X, const int* Fv, Acc& acc, ValAdd& val_add, PS* P) {
   constexpr int W = IntW<L>::W;
   using Z = fz<W>;
   enum : int { CHAIN, FWD, BWD0, BWD_D, BWD_S, LAST, DONE };
@@ -124,17 +124,17 @@ HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const f
       act = 0;
       ++e;
     } else if (phase == FWD) {
-      lhs = r == 0 ? cf : P[r - 1];
+      lhs = r == 0 ? cf : static_cast<Z>(P[r - 1]);
       rhs = X[pr[r] & 0xff];
       act = 1;
     } else if (phase == BWD0) {  // d_{k-1} = P_{k-2} (k >= 2) or d_0 = cf (k = 1)
-      lhs = k == 1 ? cf : P[k - 2];
+      lhs = k == 1 ? cf : static_cast<Z>(P[k - 2]);
       prod = false;
       act = 3;
       var = pr[k - 1] & 0xff;
       ex = pr[k - 1] >> 8;
     } else if (phase == BWD_D) {
-      lhs = P[r - 1];
+      lhs = static_cast<Z>(P[r - 1]);
       rhs = S;
       act = 3;
       var = pr[r] & 0xff;
@@ -154,8 +154,10 @@ HT_HD void sweep_monomial(const int32_t* mon_off, const uint16_t* pairs, const f
     if (act == 0) {
       cf = t;
     } else if (act == 1) {
-      P[r] = t;
-      if (r == k - 1) val_add(t);
+      if (r == k - 1)
+        val_add(t);  // the last forward product is the value; the backward sweep never reads it
+      else
+        P[r] = t;
     } else if (act == 2) {
       S = t;
     } else {
@@ -193,10 +195,9 @@ HT_HD int sweep_products(const uint16_t* pr, int k) {
 // Value (fixed-point vr, vi in frame F) and gradient of the monomials m0..m1.
 // X is anything indexable by variable that yields the converted limb string
 // (a local array, or a view of shared memory).
-template <int L, class XA, class Acc>
+template <int L, class XA, class Acc, class PS>
 HT_HD void eval_poly_int(const int32_t* mon_off, const uint16_t* pairs, const fz<IntW<L>::W>* cfz, int m0, int m1,
-                         const XA& X, int F, const int* Fv, Acc& acc, int32_t* vr, int32_t* vi,
-                         fz<IntW<L>::W>* P) {
+                         const XA& X, int F, const int* Fv, Acc& acc, int32_t* vr, int32_t* vi, PS* P) {
   constexpr int W = IntW<L>::W, WA = IntW<L>::WA;
   auto val_add = [&](const fz<W>& t) { acc_add_fast<W, WA>(vr, vi, t, 1, F); };
   for (int m = m0; m < m1; ++m) sweep_monomial<L>(mon_off, pairs, cfz, m, X, Fv, acc, val_add, P);

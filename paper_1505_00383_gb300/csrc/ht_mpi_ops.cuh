@@ -65,6 +65,41 @@ HT_HD fz<W> fixed_to_fz(const int32_t* ar_in, const int32_t* ai_in, int F) {
   return z;
 }
 
+// s times a fixed-point complex (WA limbs each, frame F), s a double, to
+// fz<W>: the product is formed exactly in WA + 2 limbs per component (s's
+// significand in a 24-bit and a 29-bit part) and cut to W limbs as
+// fixed_to_fz does.
+template <int WA, int W>
+HT_HD fz<W> fixed_scaled_to_fz(const int32_t* ar, const int32_t* ai, int F, double s) {
+  int64_t ms;
+  int es;
+  decompose(s, ms, es);  // s = ms 2^es, |ms| < 2^53
+  const bool neg = ms < 0;
+  const uint64_t u = (uint64_t)(neg ? -ms : ms);
+  const int64_t lo = (int64_t)(u & (uint64_t)MASK), hi = (int64_t)(u >> RB);
+  int64_t cr[WA + 2], ci[WA + 2];
+  for (int k = 0; k < WA + 2; ++k) cr[k] = ci[k] = 0;
+  for (int k = 0; k < WA; ++k) {  // |a_k lo| < 2^58, |a_k hi| < 2^53
+    cr[k] += (int64_t)ar[k] * lo;
+    cr[k + 1] += (int64_t)ar[k] * hi;
+    ci[k] += (int64_t)ai[k] * lo;
+    ci[k + 1] += (int64_t)ai[k] * hi;
+  }
+  if (neg)
+    for (int k = 0; k < WA + 2; ++k) {
+      cr[k] = -cr[k];
+      ci[k] = -ci[k];
+    }
+  carry<WA + 2>(cr);
+  carry<WA + 2>(ci);
+  int32_t br[WA + 2], bi[WA + 2];  // top limbs below 2^24 in magnitude
+  for (int k = 0; k < WA + 2; ++k) {
+    br[k] = (int32_t)cr[k];
+    bi[k] = (int32_t)ci[k];
+  }
+  return fixed_to_fz<WA + 2, W>(br, bi, F + es);
+}
+
 template <int W>
 HT_HD bool is_zero(const fz<W>& z) {
   int32_t o = 0;

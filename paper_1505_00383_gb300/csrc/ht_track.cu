@@ -358,9 +358,10 @@ __device__ void mgs_team(double* A, double* R, double* x, int rows, int cols, in
 }
 
 // The same least squares on the integer pipe (DD, QD): entries are read as
-// limb strings (exact conversion of the stored doubles), every dot product
-// and norm is one exact fixed-point sum of its products rounded once, 1/r_qq
-// comes from Newton's iteration for 1/sqrt, and results are stored back as
+// limb strings (from stored limb strings, or by exact conversion of stored
+// doubles), every dot product and norm is one exact fixed-point sum of its
+// products rounded once, 1/r_qq comes from Newton's iteration for 1/sqrt, and
+// results are stored back in the same form; the solution is stored as
 // doubles.  The column owner loads and normalises column q; the other warps
 // reload it after the barrier.  Layouts and R's diagonal (1/r_qq) as above.
 template <int L>
@@ -386,8 +387,45 @@ __device__ __forceinline__ void stz(double* base, int64_t e, int64_t m, int64_t 
   }
 }
 
-template <int L, int N>
-__device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
+// Storage of A and R for the integer least squares: the vertical doubles
+// (converted on every load and store) or limb strings in [entry][2W+1][m]
+// int32 words (exponent, re limbs, im limbs; loaded and stored as they are).
+template <int L>
+struct DblStore {
+  double* base;
+  int64_t m, p;
+  __device__ __forceinline__ mpi::fz<IntW<L>::W> ld(int64_t e) const { return ldz<L>(base, e, m, p); }
+  __device__ __forceinline__ void st(int64_t e, const mpi::fz<IntW<L>::W>& z) const { stz<L>(base, e, m, p, z); }
+};
+template <int L>
+struct FzStore {
+  static constexpr int W = IntW<L>::W;
+  int32_t* base;
+  int64_t m, p;
+  __device__ __forceinline__ mpi::fz<W> ld(int64_t e) const {
+    const int32_t* q = base + e * (2 * W + 1) * m + p;
+    mpi::fz<W> z;
+    z.f = q[0];
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      z.r[k] = q[(1 + k) * m];
+      z.i[k] = q[(1 + W + k) * m];
+    }
+    return z;
+  }
+  __device__ __forceinline__ void st(int64_t e, const mpi::fz<W>& z) const {
+    int32_t* q = base + e * (2 * W + 1) * m + p;
+    q[0] = z.f;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+      q[(1 + k) * m] = z.r[k];
+      q[(1 + W + k) * m] = z.i[k];
+    }
+  }
+};
+
+template <int L, int N, class ST>
+__device__ void mgs_team_int(const ST& A, const ST& R, double* x, int rows, int cols, int64_t m, int64_t p, bool act,
                              int warp, int T, int nrhs = 1, double* x2 = nullptr) {
   constexpr int W = IntW<L>::W;  // rows <= N
   using Z = mpi::fz<W>;
@@ -397,11 +435,11 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
   auto normalise = [&](int q, Z* v) {
     const Z nrm = mpi::norm2<W, N>(v, rows, S);
     const Z inv = mpi::inv_sqrt<W>(nrm, mpi::inv_sqrt_steps<W>());
-    for (int i = 0; i < rows; ++i) stz<L>(A, (int64_t)i * Wc + q, m, p, mpi::mul<W>(v[i], inv));
-    stz<L>(R, (int64_t)q * Wc + q, m, p, inv);
+    for (int i = 0; i < rows; ++i) A.st((int64_t)i * Wc + q, mpi::mul<W>(v[i], inv));
+    R.st((int64_t)q * Wc + q, inv);
   };
   if (warp == 0 && act) {  // column 0 by its owner
-    for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc, m, p);
+    for (int i = 0; i < rows; ++i) Q[i] = A.ld((int64_t)i * Wc);
     normalise(0, Q);
   }
   __syncthreads();
@@ -412,18 +450,19 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
     bool any = false;  // this warp has a column in this phase
     for (int j = q + 1; j < Wc; ++j) any = any || mgs_col_warp(j, q, T) == warp;
     if (act && any) {
-      for (int i = 0; i < rows; ++i) Q[i] = ldz<L>(A, (int64_t)i * Wc + q, m, p);
+      for (int i = 0; i < rows; ++i) Q[i] = A.ld((int64_t)i * Wc + q);
       for (int j = q + 1; j < Wc; ++j) {
         if (mgs_col_warp(j, q, T) != warp) continue;
-        for (int i = 0; i < rows; ++i) col[i] = ldz<L>(A, (int64_t)i * Wc + j, m, p);
+        for (int i = 0; i < rows; ++i) col[i] = A.ld((int64_t)i * Wc + j);
         const Z r = mpi::dot_conj<W, N>(Q, col, rows, S);
-        stz<L>(R, (int64_t)q * Wc + j, m, p, r);
+        R.st((int64_t)q * Wc + j, r);
         mpi::sub_scaled<W>(col, r, Q, rows);
-        for (int i = 0; i < rows; ++i) stz<L>(A, (int64_t)i * Wc + j, m, p, col[i]);
+        for (int i = 0; i < rows; ++i) A.st((int64_t)i * Wc + j, col[i]);
         if (j == q + 1 && j < cols) {
           // the pivot column from its stored values, as the owner's reload
-          // would give: the limb strings of the doubles just written
-          for (int i = 0; i < rows; ++i) col[i] = ldz<L>(A, (int64_t)i * Wc + j, m, p);
+          // would give (for stored doubles the limb strings of the doubles
+          // just written; stored limb strings come back as they were)
+          for (int i = 0; i < rows; ++i) col[i] = A.ld((int64_t)i * Wc + j);
           normalise(j, col);
         }
       }
@@ -434,9 +473,9 @@ __device__ void mgs_team_int(double* A, double* R, double* x, int rows, int cols
   for (int r = warp; act && r < nrhs; r += T) {
     for (int q = cols - 1; q >= 0; --q) {
       int k = 0;
-      S[k++] = ldz<L>(R, (int64_t)q * Wc + cols + r, m, p);
-      for (int j = q + 1; j < cols; ++j) S[k++] = mpi::mul<W>(ldz<L>(R, (int64_t)q * Wc + j, m, p), col[j]);
-      col[q] = mpi::mul<W>(mpi::first_minus_rest<W, N + 1>(S, k), ldz<L>(R, (int64_t)q * Wc + q, m, p));
+      S[k++] = R.ld((int64_t)q * Wc + cols + r);
+      for (int j = q + 1; j < cols; ++j) S[k++] = mpi::mul<W>(R.ld((int64_t)q * Wc + j), col[j]);
+      col[q] = mpi::mul<W>(mpi::first_minus_rest<W, N + 1>(S, k), R.ld((int64_t)q * Wc + q));
     }
     double* xs = r == 0 ? x : x2;
     for (int q = 0; q < cols; ++q) stz<L>(xs, q, m, p, col[q]);
@@ -449,7 +488,8 @@ template <int L, bool INT>
 __global__ void __launch_bounds__(32) mgs_kernel(double* A, double* R, double* x, int rows, int cols, int64_t n_sys) {
   int64_t p = (int64_t)blockIdx.x * 32 + threadIdx.x;
   if constexpr (INT)
-    mgs_team_int<L, kIntMaxVars>(A, R, x, rows, cols, n_sys, p, p < n_sys, 0, 1);
+    mgs_team_int<L, kIntMaxVars>(DblStore<L>{A, n_sys, p}, DblStore<L>{R, n_sys, p}, x, rows, cols, n_sys, p,
+                                 p < n_sys, 0, 1);
   else
     mgs_team<L>(A, R, x, rows, cols, n_sys, p, p < n_sys, 0, 1);
 }
@@ -486,6 +526,17 @@ __device__ __noinline__ double learned_step(const TrackArgs& a, MlpWarpSmem& sta
 // of the evaluation and of MGS are sized by it).
 constexpr int kIntMaxTrack = 32;
 
+// An L-limb complex as a limb string (exact).
+template <int L>
+__device__ __forceinline__ mpi::fz<IntW<L>::W> fz_of(const cx<L>& z) {
+  double re[L], im[L];
+#pragma unroll
+  for (int l = 0; l < L; ++l) {
+    re[l] = r_limb(z.re, l);
+    im[l] = r_limb(z.im, l);
+  }
+  return mpi::from_doubles<IntW<L>::W, L>(re, im);
+}
 template <int L>
 __device__ __forceinline__ cx<L> cx_from(const double* re, const double* im) {
   if constexpr (L == 1) {
@@ -508,6 +559,7 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
   __shared__ double sh_h[32];       // learned step of each lane's path
   __shared__ double sh_alpha[32];   // learned tangent correction of each lane's path
   __shared__ long long sh_slot[32]; // trace record slot of each lane's path (-1: none)
+  __shared__ double sh_w[8][L][32]; // extrapolation weights of each lane's step, [point][limb][lane]
   // The network's weights are read from the device image (L1/L2): staging
   // them in shared memory would enlarge the shared-memory carveout and take
   // L1 capacity from the Newton workspace.  Only warp 0's sample staging
@@ -525,6 +577,10 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
   const int64_t m = a.m;
   const int count = *a.count_in;
   const int64_t rowA = (int64_t)W * 2 * L * m;  // doubles per row of A
+  // QD with integer evaluation keeps A and R as limb strings ([entry][2W+1][m]
+  // words) from the evaluation through the least squares: no conversions
+  constexpr bool FZ = INT && L == 4;
+  const int64_t rowZ = (int64_t)W * (2 * IntW<L>::W + 1) * m;  // words per row of A
   PolyView v;
   v.mon_off = a.mon_off;
   v.pairs = a.pairs;
@@ -598,14 +654,36 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
         }
       }
       // ---- A: predictor (first Newton round of a step) or polish copy
+      // The extrapolation weights (a product and a QD division per history
+      // point) are dealt to the warps, one point each, and shared through
+      // shared memory: every warp used to compute all of them, contending
+      // for the FP64 pipe.  Each weight is the same sequence of operations
+      // as before, so the predicted points are bitwise unchanged.
+      const bool herm = start && pmode == 2 && ntan >= 2 && nh >= 2;
+      const bool euler = start && !herm && pmode >= 1 && ntan >= 1;
+      const int mm = !start ? 0 : ((herm || euler) ? 0 : (pmode >= 1 ? 1 : min(nh, a.prm.max_order + 1)));
+      const int base = nh - mm;
       if (start) {
         double step = fmin(h, 1.0 - t);
         t1 = (step >= 1.0 - t) ? 1.0 : t + step;
+        for (int j = warp; j < mm; j += T) {
+          rl<L> num = r_from<L>(1.0), den = r_from<L>(1.0);
+          double tj = a.ht[(int64_t)(base + j) * m + p];
+          for (int i = 0; i < mm; ++i) {
+            if (i == j) continue;
+            double ti = a.ht[(int64_t)(base + i) * m + p];
+            num = r_mul(num, r_diff<L>(t1, ti));
+            den = r_mul(den, r_diff<L>(tj, ti));
+          }
+          const rl<L> wj = r_div(num, den);
+#pragma unroll
+          for (int l = 0; l < L; ++l) sh_w[j][l][lane] = r_limb(wj, l);
+        }
+      }
+      __syncthreads();
+      if (start) {
         // tangent predictors: cubic Hermite on the last two points and their
         // tangents, Euler on the last one; until a tangent exists, x itself
-        const bool herm = pmode == 2 && ntan >= 2 && nh >= 2, euler = !herm && pmode >= 1 && ntan >= 1;
-        const int mm = (herm || euler) ? 0 : (pmode >= 1 ? 1 : min(nh, a.prm.max_order + 1));
-        const int base = nh - mm;
         rl<L> ca = r_from<L>(0.0), cb = r_from<L>(0.0), cc = r_from<L>(0.0), cd = r_from<L>(0.0);
         if (herm) {  // x0, v0 at s0 = ht[nh-2]; x1, v1 at s1 = ht[nh-1]
           const double s0 = a.ht[(int64_t)(nh - 2) * m + p], s1 = a.ht[(int64_t)(nh - 1) * m + p];
@@ -621,15 +699,10 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
         }
         rl<L> w[8];
         for (int j = 0; j < mm; ++j) {
-          rl<L> num = r_from<L>(1.0), den = r_from<L>(1.0);
-          double tj = a.ht[(int64_t)(base + j) * m + p];
-          for (int i = 0; i < mm; ++i) {
-            if (i == j) continue;
-            double ti = a.ht[(int64_t)(base + i) * m + p];
-            num = r_mul(num, r_diff<L>(t1, ti));
-            den = r_mul(den, r_diff<L>(tj, ti));
-          }
-          w[j] = r_div(num, den);
+          double wl[L];
+#pragma unroll
+          for (int l = 0; l < L; ++l) wl[l] = sh_w[j][l][lane];
+          w[j] = r_of<L>(wl);
         }
         for (int i = warp; i < n; i += T) {
           cx<L> acc = czero<L>();
@@ -676,21 +749,29 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
       }
       if (act) {
         cx<L> gs = cscale_r(gamma, r_diff<L>(1.0, tt));
-        Z P[INT ? kIntMaxTrack : 1];
+        mpi::fzs<IntW<L>::W> P[INT ? kIntMaxTrack : 1];
         const SmemPoints<L> X{xs_int, lane};
         const SmemLog lg{lgs_int, lane};
         for (int j = warp; j < n; j += T) {
           double* Arow = a.A + (int64_t)j * rowA;
+          const FzStore<L> Zrow{reinterpret_cast<int32_t*>(a.A) + (int64_t)j * rowZ, m, p};
           cx<L> fj;
           if constexpr (INT) {
             double vre[L], vim[L];
-            int_row<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
-                       __ldg(a.poly_off + j + 1), X, lg, n, Arow, m, p, vre, vim, P);
+            // the row comes out as tt times the gradient, scaled in the
+            // exact fixed-point sums (one rounding, no FP64 multiplies); for
+            // QD as the limb strings the integer least squares reads
+            if constexpr (FZ)
+              int_row_fz<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
+                            __ldg(a.poly_off + j + 1), X, lg, n, Zrow.base, m, p, vre, vim, P, tt);
+            else
+              int_row<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
+                         __ldg(a.poly_off + j + 1), X, lg, n, Arow, m, p, vre, vim, P, tt);
             fj = cx_from<L>(vre, vim);
           } else {
             fj = eval_poly<L>(v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), n, p, Arow);
+            for (int i = 0; i < n; ++i) st<L>(Arow, i, m, p, cscale(ld<L>(Arow, i, m, p), tt));
           }
-          for (int i = 0; i < n; ++i) st<L>(Arow, i, m, p, cscale(ld<L>(Arow, i, m, p), tt));
           const int d = __ldg(a.deg + j);
           cx<L> xj = ld<L>(a.xp, j, m, p);
           cx<L> xd1 = creal<L>(1.0);
@@ -698,11 +779,17 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
           cx<L> gval = csub(cmul(xd1, xj), creal<L>(1.0));
           cx<L> hj = cadd(cmul(gs, gval), cscale(fj, tt));
           cx<L> dg = cmul(gs, cscale(xd1, (double)d));
-          st<L>(Arow, j, m, p, cadd(ld<L>(Arow, j, m, p), dg));
           cx<L> mh = czero<L>();
           mh = csub(mh, hj);
-          st<L>(Arow, n, m, p, mh);
-          if (nrhs == 2) st<L>(Arow, n + 1, m, p, csub(cmul(gamma, gval), fj));  // -dh/dt = gamma g - f
+          if constexpr (FZ) {
+            Zrow.st(j, mpi::add<IntW<L>::W>(Zrow.ld(j), fz_of<L>(dg)));
+            Zrow.st(n, fz_of<L>(mh));
+            if (nrhs == 2) Zrow.st(n + 1, fz_of<L>(csub(cmul(gamma, gval), fj)));  // -dh/dt = gamma g - f
+          } else {
+            st<L>(Arow, j, m, p, cadd(ld<L>(Arow, j, m, p), dg));
+            st<L>(Arow, n, m, p, mh);
+            if (nrhs == 2) st<L>(Arow, n + 1, m, p, csub(cmul(gamma, gval), fj));  // -dh/dt = gamma g - f
+          }
           pres = nanmax(pres, cfinite(hj) ? cabs_lead(hj) : __longlong_as_double(0x7ff8000000000000LL));
         }
       }
@@ -711,8 +798,10 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
       // QD solves on the integer pipe; a DD complex product is only 38 FP64
       // instructions, and there the FP64 MGS was measured faster (1.6 s
       // against 3.1 s for the whole n = 12, 4,096-path DD run)
-      if constexpr (INT && L == 4)
-        mgs_team_int<L, kIntMaxTrack>(a.A, a.R, a.dx, n, n, m, p, act, warp, T, nrhs, a.tdx);
+      if constexpr (FZ)
+        mgs_team_int<L, kIntMaxTrack>(FzStore<L>{reinterpret_cast<int32_t*>(a.A), m, p},
+                                      FzStore<L>{reinterpret_cast<int32_t*>(a.R), m, p}, a.dx, n, n, m, p, act, warp,
+                                      T, nrhs, a.tdx);
       else
         mgs_team<L>(a.A, a.R, a.dx, n, n, m, p, act, warp, T, nrhs, a.tdx);
       // ---- D: x <- x + dx on this warp's coordinates; partial norms

@@ -304,8 +304,14 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
     return o;
   };
   const int nrhs = P.predictor > 0 ? 2 : 1;  // the tangent predictors add J v = -dh/dt
+  // DD and QD (n <= 32) evaluate f and solve the Newton systems on the
+  // integer pipe unless an FP64 variant was chosen for this system
+  // (ht_set_eval_config 0 or 1); QD then keeps A and R as limb strings of
+  // 2 W + 1 = 17 int32 words an entry (68 bytes against 64 for the doubles)
+  const bool int_eval = L > 1 && s->d_coef_fz && n <= 32 && (s->eval_variant == -1 || s->eval_variant == 2);
+  const size_t ab = (int_eval && L == 4) ? (size_t)17 * 4 * m : cxb;  // bytes of one entry of A and R
   size_t o_xp = take(n * cxb), o_hx = take((size_t)cap * n * cxb), o_ht = take((size_t)cap * m * 8),
-         o_A = take((size_t)n * (n + nrhs) * cxb), o_R = take((size_t)n * (n + nrhs) * cxb), o_dx = take(n * cxb),
+         o_A = take((size_t)n * (n + nrhs) * ab), o_R = take((size_t)n * (n + nrhs) * ab), o_dx = take(n * cxb),
          o_tx = P.predictor > 0 ? take((size_t)cap * n * cxb) : 0, o_tdx = P.predictor > 0 ? take(n * cxb) : 0,
          o_ntan = take(m),
          o_h = take(m * 8), o_t1 = take(m * 8), o_it = take(m), o_ph = take(m), o_nh = take(m),
@@ -323,10 +329,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.coef = s->d_coef;
   a.cfz = s->d_coef_fz;
   a.clg = s->d_coef_lg;
-  // DD and QD (n <= 32) evaluate f and solve the Newton systems on the
-  // integer pipe unless an FP64 variant was chosen for this system
-  // (ht_set_eval_config 0 or 1)
-  a.int_eval = L > 1 && s->d_coef_fz && n <= 32 && (s->eval_variant == -1 || s->eval_variant == 2);
+  a.int_eval = int_eval;
   a.deg = (const int32_t*)(w + o_deg);
   a.gamma_re = gamma[0];
   a.gamma_im = gamma[1];

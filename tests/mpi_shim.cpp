@@ -106,7 +106,7 @@ int mpi_dot_fast(int L, int64_t n, int k, const double* a, const double* b, cons
 // the accumulator's last limb (they may differ by the truncation of the
 // dropped bits: the generic version truncates each limb toward zero).
 template <int W, int WA, int L>
-static int64_t compare_acc(int64_t n, const double* in, int smin, int smax) {
+static int64_t compare_acc(int64_t n, const double* in, int smin, int smax, int e) {
   int64_t worst = 0;
   for (int64_t q = 0; q < n; ++q) {
     fz<W> z0 = from_doubles<W, L>(in + q * 2 * L, in + q * 2 * L + L);
@@ -136,14 +136,17 @@ static int64_t compare_acc(int64_t n, const double* in, int smin, int smax) {
         const int64_t mi = z.i[top] < 0 ? -(int64_t)z.i[top] : z.i[top];
         int b = 0;
         while (((mr > mi ? mr : mi) >> b) != 0) ++b;
-        const int bits = z.f + RB * top + b + 2 + 1;  // bit length of 3 |z|, bound from above
+        const int ae = e < 0 ? -e : e;
+        int eb = 0;
+        while ((ae >> eb) != 0) ++eb;
+        const int bits = z.f + RB * top + b + eb + 1;  // bit length of |e z|, bound from above
         if (bits > RB * (WA - 1) + 28 + F) continue;
       }
       int32_t a1[WA] = {0}, b1[WA] = {0}, a2[WA] = {0}, b2[WA] = {0};
       a1[0] = a2[0] = 12345;
       b1[WA - 1] = b2[WA - 1] = -7;
-      acc_add<W, WA>(a1, b1, z, 3, F);
-      acc_add_fast<W, WA>(a2, b2, z, 3, F);
+      acc_add<W, WA>(a1, b1, z, e, F);
+      acc_add_fast<W, WA>(a2, b2, z, e, F);
       // exact difference of the values, limb by limb from the top (it is small)
       long double dr = 0, di = 0;
       for (int k = WA - 1; k >= 0; --k) {
@@ -160,9 +163,9 @@ static int64_t compare_acc(int64_t n, const double* in, int smin, int smax) {
   }
   return worst;
 }
-extern "C" int64_t mpi_compare_acc(int L, int64_t n, const double* in, int smin, int smax) {
-  if (L == 2) return compare_acc<5, 4, 2>(n, in, smin, smax);
-  if (L == 4) return compare_acc<8, 8, 4>(n, in, smin, smax);
+extern "C" int64_t mpi_compare_acc(int L, int64_t n, const double* in, int smin, int smax, int e) {
+  if (L == 2) return compare_acc<5, 4, 2>(n, in, smin, smax, e);
+  if (L == 4) return compare_acc<8, 8, 4>(n, in, smin, smax, e);
   return -1;
 }
 
@@ -338,5 +341,24 @@ extern "C" int mpi_mgs(int L, int rows, int cols, int64_t n_sys, const double* A
     else if (L == 1) mgs_seq<3, 1>(rows, cols, Ab + s * sa, x + s * sx);
     else return -1;
   }
+  return 0;
+}
+
+// s * a for fixed-point limb strings a (n rows of WA int32 limbs, frame F)
+// and doubles s[n], to L doubles per row (out), and the unscaled conversion
+// of the same strings (plain) for comparison.
+template <int WA, int L>
+static void scaled(int64_t n, const int32_t* a, int F, const double* s, double* out, double* plain) {
+  for (int64_t q = 0; q < n; ++q) {
+    fixed_scaled_to_doubles<WA, L>(a + q * WA, F, s[q], out + q * L);
+    fixed_to_doubles<WA, L>(a + q * WA, F, plain + q * L);
+  }
+}
+extern "C" int mpi_scaled_convert(int L, int64_t n, const int32_t* a, int F, const double* s, double* out,
+                                  double* plain) {
+  if (L == 1) scaled<2, 1>(n, a, F, s, out, plain);
+  else if (L == 2) scaled<4, 2>(n, a, F, s, out, plain);
+  else if (L == 4) scaled<8, 4>(n, a, F, s, out, plain);
+  else return -1;
   return 0;
 }

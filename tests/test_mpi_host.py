@@ -116,18 +116,24 @@ def test_fixed_point_sums_with_cancellation(oracle_lib, shim, L, fast):
     assert np.all(err <= 2.0 ** (-53 * L + 12) * absum), np.max(err / absum)
 
 
+@pytest.mark.parametrize("e", [3, 1, -3, 4, -5, 127])
 @pytest.mark.parametrize("L", [2, 4])
-def test_shift_accumulation_equals_generic(shim, L):
+def test_shift_accumulation_equals_generic(shim, L, e):
     """The single-shift accumulation gives the same limbs as the generic
     per-limb one for right and left shifts (frames slightly above the
     accumulator's included) wherever its precondition holds: the term times
     its factor below the top limb's bit 28 (for DD, whose accumulator has one
-    limb fewer than a term, that rules out every left shift)."""
-    shim.mpi_compare_acc.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_int]
+    limb fewer than a term, that rules out every left shift).  Factors up to
+    3 in magnitude take the 32-bit sums, larger ones the 64-bit sums."""
+    shim.mpi_compare_acc.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                     ctypes.c_int]
     shim.mpi_compare_acc.restype = ctypes.c_int64
     x = _complex(77 + L, 200, L, spread=3)
-    worst = shim.mpi_compare_acc(L, x.shape[0], _p(x), -20, 29 * 9)
-    assert 0 <= worst <= 2 * 8, worst  # within a few units of the last limb
+    worst = shim.mpi_compare_acc(L, x.shape[0], _p(x), -20, 29 * 9, e)
+    # the single shift truncates the term before the factor (at most |e| units
+    # of the last limb); the generic routine truncates each of the W <= 8
+    # shifted limbs of e z
+    assert 0 <= worst <= abs(e) + 8, worst
 
 
 @pytest.mark.parametrize("L", [1, 2, 4])
@@ -248,3 +254,36 @@ def test_least_squares_on_limb_strings_matches_oracle(oracle_lib, shim, L, rows,
         scale = np.max(np.abs(r))
         e = np.max(_cerr(oracle_lib, x[s], ref[s]))
         assert e <= 64 * cond * cond * _unit(L) * scale * rows, (s, e, cond)
+
+
+@pytest.mark.parametrize("L", [1, 2, 4])
+def test_scaled_conversion_is_the_truncated_exact_product(shim, L):
+    """s a for a fixed-point string a and a double s, converted to L doubles:
+    the doubles' exact sum is the exact product a s truncated to the leading
+    53 L bits (so it lies within 2^(1 - 53 L) |a s| below |a s|), and for s = 1
+    the doubles are those of the plain conversion.  Exact rationals on the
+    Python side; strings with a negative top limb and scales of every sign
+    and binade included."""
+    from fractions import Fraction
+    WA = {1: 2, 2: 4, 4: 8}[L]
+    F = -29 * (WA - 1) - 3
+    rng = np.random.default_rng(500 + L)
+    n = 400
+    a = rng.integers(0, 1 << 29, size=(n, WA)).astype(np.int32)
+    a[:, -1] = rng.integers(-(1 << 27), 1 << 27, size=n)
+    a[::7, :-1] = 0  # sparse strings: a single top limb
+    s = rng.uniform(-1.0, 1.0, n) * np.exp2(rng.integers(-60, 60, n))
+    s[:5] = [1.0, -1.0, 0.5, 1.0 - 2.0 ** -53, 0.0]
+    out = np.zeros((n, L))
+    plain = np.zeros((n, L))
+    shim.mpi_scaled_convert.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                                        ctypes.c_void_p, ctypes.c_void_p]
+    assert shim.mpi_scaled_convert(L, n, _p(a), F, _p(s), _p(out), _p(plain)) == 0
+    for q in range(n):
+        val = sum(Fraction(int(a[q, k])) * Fraction(2) ** (29 * k) for k in range(WA)) * Fraction(2) ** F
+        exact = val * Fraction(float(s[q]))
+        got = sum(Fraction(float(d)) for d in out[q])
+        assert abs(got) <= abs(exact)  # truncation toward zero
+        assert abs(exact - got) <= abs(exact) * Fraction(2) ** (1 - 53 * L), (q, float(exact), float(got))
+        if s[q] == 1.0:
+            assert np.array_equal(out[q], plain[q])
