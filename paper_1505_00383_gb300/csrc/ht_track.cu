@@ -593,7 +593,16 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
     g.im = r_from<L>(a.gamma_im);
     return g;
   }();
-  for (int64_t g = blockIdx.x; g * 32 < count; g += gridDim.x) {
+  // Groups of 32 active paths are taken from a queue (one counter per
+  // launch, zeroed by the compaction before it): a CTA whose groups finish
+  // early takes more, instead of a fixed share of them.
+  __shared__ int sh_group;
+  for (;;) {
+    if (threadIdx.x == 0) sh_group = atomicAdd(a.queue, 1);
+    __syncthreads();
+    const int64_t g = sh_group;
+    __syncthreads();  // every thread has read the group before the next take
+    if (g * 32 >= count) break;
     const int64_t slot = g * 32 + lane;
     const int64_t p = slot < count ? a.idx_in[slot] : -1;
     for (int iter = 0; iter < a.iters; ++iter) {
@@ -747,26 +756,64 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
         }
         __syncthreads();
       }
-      if (act) {
+      if constexpr (FZ) {
+       if (act) {
+        // QD on the integer pipe throughout: the row, the start system's
+        // terms and the homotopy in limb-string arithmetic (a QD complex
+        // product on the FP64 pipe costs about 30 times a limb-string one)
+        using ZW = mpi::fz<IntW<L>::W>;
+        constexpr int WZ = IntW<L>::W;
+        mpi::fzs<IntW<L>::W> P[INT ? kIntMaxTrack : 1];
+        const SmemPoints<L> X{xs_int, lane};
+        const SmemLog lg{lgs_int, lane};
+        const ZW gz = fz_of<L>(gamma);
+        const ZW gsz = fz_of<L>(cscale_r(gamma, r_diff<L>(1.0, tt)));  // gamma (1 - tt)
+        const ZW ttz = mpi::from_real<WZ>(tt), one = mpi::from_real<WZ>(1.0);
+        for (int j = warp; j < n; j += T) {
+          const FzStore<L> Zrow{reinterpret_cast<int32_t*>(a.A) + (int64_t)j * rowZ, m, p};
+          double vre[L], vim[L];
+          // the row comes out as tt times the gradient, scaled in the exact
+          // fixed-point sums, as the limb strings the least squares reads
+          int_row_fz<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
+                        __ldg(a.poly_off + j + 1), X, lg, n, Zrow.base, m, p, vre, vim, P, tt);
+          const ZW fj = mpi::from_doubles<WZ, L>(vre, vim);
+          const int d = __ldg(a.deg + j);
+          const ZW xj = X[j];
+          ZW xd1 = one;  // x_j^(d-1)
+          for (int e = 0; e < d - 1; ++e) xd1 = e == 0 ? xj : mpi::mul<WZ>(xd1, xj);
+          const ZW gval = mpi::sub<WZ>(mpi::mul<WZ>(xd1, xj), one);  // x_j^d - 1
+          ZW t2[2] = {mpi::mul<WZ>(gsz, gval), mpi::mul<WZ>(ttz, fj)};
+          const int e_add[2] = {1, 1}, e_neg[2] = {-1, -1};
+          const ZW hj = mpi::sum<WZ, 2>(t2, e_add, 2);
+          const ZW mh = mpi::sum<WZ, 2>(t2, e_neg, 2);
+          const int e_d[1] = {d};
+          const ZW dg = mpi::mul<WZ>(gsz, mpi::sum<WZ, 1>(&xd1, e_d, 1));  // gamma (1 - tt) d x_j^(d-1)
+          Zrow.st(j, mpi::add<WZ>(Zrow.ld(j), dg));
+          Zrow.st(n, mh);
+          if (nrhs == 2) Zrow.st(n + 1, mpi::sub<WZ>(mpi::mul<WZ>(gz, gval), fj));  // -dh/dt = gamma g - f
+          // the residual's modulus from its leading limb; a non-finite
+          // coordinate (which limb strings cannot carry) makes it NaN
+          double hr, hi;
+          mpi::to_doubles<WZ, 1>(hj, &hr, &hi);
+          const bool fin = cfinite(ld<L>(a.xp, j, m, p)) && isfinite(hr) && isfinite(hi);
+          pres = nanmax(pres, fin ? __dsqrt_rn(__dadd_rn(__dmul_rn(hr, hr), __dmul_rn(hi, hi)))
+                                  : __longlong_as_double(0x7ff8000000000000LL));
+        }
+       }
+      } else if (act) {
         cx<L> gs = cscale_r(gamma, r_diff<L>(1.0, tt));
         mpi::fzs<IntW<L>::W> P[INT ? kIntMaxTrack : 1];
         const SmemPoints<L> X{xs_int, lane};
         const SmemLog lg{lgs_int, lane};
         for (int j = warp; j < n; j += T) {
           double* Arow = a.A + (int64_t)j * rowA;
-          const FzStore<L> Zrow{reinterpret_cast<int32_t*>(a.A) + (int64_t)j * rowZ, m, p};
           cx<L> fj;
           if constexpr (INT) {
             double vre[L], vim[L];
             // the row comes out as tt times the gradient, scaled in the
-            // exact fixed-point sums (one rounding, no FP64 multiplies); for
-            // QD as the limb strings the integer least squares reads
-            if constexpr (FZ)
-              int_row_fz<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
-                            __ldg(a.poly_off + j + 1), X, lg, n, Zrow.base, m, p, vre, vim, P, tt);
-            else
-              int_row<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
-                         __ldg(a.poly_off + j + 1), X, lg, n, Arow, m, p, vre, vim, P, tt);
+            // exact fixed-point sums (one rounding, no FP64 multiplies)
+            int_row<L>(a.mon_off, a.pairs, static_cast<const Z*>(a.cfz), a.clg, __ldg(a.poly_off + j),
+                       __ldg(a.poly_off + j + 1), X, lg, n, Arow, m, p, vre, vim, P, tt);
             fj = cx_from<L>(vre, vim);
           } else {
             fj = eval_poly<L>(v, __ldg(a.poly_off + j), __ldg(a.poly_off + j + 1), n, p, Arow);
@@ -779,17 +826,11 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
           cx<L> gval = csub(cmul(xd1, xj), creal<L>(1.0));
           cx<L> hj = cadd(cmul(gs, gval), cscale(fj, tt));
           cx<L> dg = cmul(gs, cscale(xd1, (double)d));
+          st<L>(Arow, j, m, p, cadd(ld<L>(Arow, j, m, p), dg));
           cx<L> mh = czero<L>();
           mh = csub(mh, hj);
-          if constexpr (FZ) {
-            Zrow.st(j, mpi::add<IntW<L>::W>(Zrow.ld(j), fz_of<L>(dg)));
-            Zrow.st(n, fz_of<L>(mh));
-            if (nrhs == 2) Zrow.st(n + 1, fz_of<L>(csub(cmul(gamma, gval), fj)));  // -dh/dt = gamma g - f
-          } else {
-            st<L>(Arow, j, m, p, cadd(ld<L>(Arow, j, m, p), dg));
-            st<L>(Arow, n, m, p, mh);
-            if (nrhs == 2) st<L>(Arow, n + 1, m, p, csub(cmul(gamma, gval), fj));  // -dh/dt = gamma g - f
-          }
+          st<L>(Arow, n, m, p, mh);
+          if (nrhs == 2) st<L>(Arow, n + 1, m, p, csub(cmul(gamma, gval), fj));  // -dh/dt = gamma g - f
           pres = nanmax(pres, cfinite(hj) ? cabs_lead(hj) : __longlong_as_double(0x7ff8000000000000LL));
         }
       }
@@ -973,7 +1014,7 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
 __global__ void __launch_bounds__(1024) compact_kernel(const int32_t* __restrict__ idx_in,
                                                        const int32_t* __restrict__ count_in,
                                                        const int8_t* __restrict__ status, int32_t* __restrict__ idx_out,
-                                                       int32_t* __restrict__ count_out) {
+                                                       int32_t* __restrict__ count_out, int32_t* __restrict__ reset) {
   __shared__ int wsum[32];
   __shared__ int base;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1002,7 +1043,10 @@ __global__ void __launch_bounds__(1024) compact_kernel(const int32_t* __restrict
     if (threadIdx.x == 0) base += wsum[31];
     __syncthreads();
   }
-  if (threadIdx.x == 0) *count_out = base;
+  if (threadIdx.x == 0) {
+    *count_out = base;
+    if (reset) *reset = 0;
+  }
 }
 
 #endif
@@ -1042,8 +1086,8 @@ int launch_mlp_image(void* img, const __nv_bfloat16* wbf, const float* master, c
 }
 
 int launch_compact(const int32_t* idx_in, const int32_t* count_in, const int8_t* status, int32_t* idx_out,
-                   int32_t* count_out, cudaStream_t st) {
-  compact_kernel<<<1, 1024, 0, st>>>(idx_in, count_in, status, idx_out, count_out);
+                   int32_t* count_out, cudaStream_t st, int32_t* reset) {
+  compact_kernel<<<1, 1024, 0, st>>>(idx_in, count_in, status, idx_out, count_out, reset);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? HT_OK : cuda_fail(e, "compact launch");
 }

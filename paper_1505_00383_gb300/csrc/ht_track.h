@@ -67,6 +67,7 @@ struct TrackArgs {
   int polish_only;         // start every path at t = 1 in the polish phase
   const int32_t* idx_in;   // active path indices of this launch
   const int32_t* count_in; // their number (device)
+  int32_t* queue;          // next 32-path group to take (device; zero at launch)
   int32_t* idx0;           // init: identity index list
   int32_t* count0;
   // last step summary (features of the learned step) and learned-step state
@@ -109,7 +110,9 @@ int launch_scatter_l(int n, const int32_t* ids, const int32_t* count, int64_t ca
                      const double* ts, double* xd, int8_t* sd, double* td, int64_t m, cudaStream_t st);
 int launch_mlp_image(void* img, const __nv_bfloat16* wbf, const float* master, cudaStream_t st);
 size_t mlp_image_bytes();
+// Stable compaction of idx_in[0..*count_in) to the paths with status 0;
+// reset (if given) is set to zero as well (the next launch's group queue).
 int launch_compact(const int32_t* idx_in, const int32_t* count_in, const int8_t* status, int32_t* idx_out,
-                   int32_t* count_out, cudaStream_t st);
+                   int32_t* count_out, cudaStream_t st, int32_t* reset = nullptr);
 
 }  // namespace ht

@@ -316,7 +316,7 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
          o_ntan = take(m),
          o_h = take(m * 8), o_t1 = take(m * 8), o_it = take(m), o_ph = take(m), o_nh = take(m),
          o_steps = take(m * 4), o_rej = take(m * 4), o_newt = take(m * 4), o_idx0 = take((m + 1) * 4),
-         o_idx1 = take((m + 1) * 4), o_cnt = take(2 * 4), o_deg = take(n * 4), o_ldx = take(m * 8),
+         o_idx1 = take((m + 1) * 4), o_cnt = take(4 * 4), o_deg = take(n * 4), o_ldx = take(m * 8),
          o_lres = take(m * 8), o_lits = take(m), o_lrej = take(m), o_fb = take(m),
          o_img = IO.mlp ? take(mlp_image_bytes()) : 0;
   int rc = ensure_track_ws(s, off, st);
@@ -359,6 +359,13 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   a.newton = (int32_t*)(w + o_newt);
   int32_t* idx[2] = {(int32_t*)(w + o_idx0), (int32_t*)(w + o_idx1)};
   int32_t* cnt[2] = {(int32_t*)(w + o_cnt), (int32_t*)(w + o_cnt) + 1};
+  // group queues of the track launches (alternating; each compaction zeroes
+  // the next launch's), zero before the first
+  int32_t* queue[2] = {(int32_t*)(w + o_cnt) + 2, (int32_t*)(w + o_cnt) + 3};
+  {
+    cudaError_t eq = cudaMemsetAsync(queue[0], 0, 2 * sizeof(int32_t), st);
+    if (eq != cudaSuccess) return cuda_fail(eq, "ht_track_paths: queue");
+  }
   a.idx0 = idx[0];
   a.count0 = cnt[0];
   a.last_dx = (double*)(w + o_ldx);
@@ -455,9 +462,12 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
         TrackArgs ar = a;
         ar.idx_in = idx[r & 1];
         ar.count_in = cnt[r & 1];
+        ar.queue = queue[r & 1];
         ar.iters = iters;
         crc = by_limbs(L, [&](auto c) { return launch_track_l<decltype(c)::value>(ar, team, groups, cs); });
-        if (crc == HT_OK) crc = launch_compact(idx[r & 1], cnt[r & 1], status, idx[(r + 1) & 1], cnt[(r + 1) & 1], cs);
+        if (crc == HT_OK)
+          crc = launch_compact(idx[r & 1], cnt[r & 1], status, idx[(r + 1) & 1], cnt[(r + 1) & 1], cs,
+                               queue[(r + 1) & 1]);
       }
       graph = nullptr;
       cudaError_t ee = cudaStreamEndCapture(cs, &graph);
