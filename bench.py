@@ -434,13 +434,12 @@ def quality_up(ht, torch, world, name="batched_n12_dd", Lh=2, h_min=1e-6):
 # The n = 16 network trains on traces of 200 seeded systems of the workload's
 # shape (32 paths each, 20 epochs); on the held-out system that gives 334 Newton
 # rounds per path against 343 for 6 systems x 256 paths (same sample count
-# within 4x), for about 70 s of trace collection.  The launch shape is tuned
-# on a sample with more 32-path groups than SMs (16,384 paths for n = 16): on
-# 4,096 paths (128 groups) 16-warp teams win, and they ran the 65,536-path
-# arms 20 % slower than 8-warp teams.
+# within 4x), for about 70 s of trace collection.  The n = 16 launch shape is
+# tuned on all 65,536 paths: on samples of 4,096 and 16,384 paths 16-warp
+# teams won, and they ran the 65,536-path arms 20 % slower than 8-warp teams.
 LEARNED_CASES = {
     "learned_n16_d": dict(limbs=1, check_limbs=2, eval_seed=3500, train_seeds=range(3000, 3200), train_paths=32,
-                         epochs=20, warm_paths=None, tune_paths=16384),
+                         epochs=20, warm_paths=None, tune_paths=65536),
     "stress_n10_qd": dict(limbs=4, check_limbs=0, eval_seed=4000, train_seeds=range(4100, 4106), train_paths=256,
                          epochs=30, warm_paths=1024, tune_paths=1024),
 }

@@ -577,9 +577,10 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
   const int64_t m = a.m;
   const int count = *a.count_in;
   const int64_t rowA = (int64_t)W * 2 * L * m;  // doubles per row of A
-  // QD with integer evaluation keeps A and R as limb strings ([entry][2W+1][m]
-  // words) from the evaluation through the least squares: no conversions
-  constexpr bool FZ = INT && L == 4;
+  // DD and QD with integer evaluation keep A and R as limb strings
+  // ([entry][2W+1][m] words) from the evaluation through the least squares:
+  // no conversions
+  constexpr bool FZ = INT && L >= 2;
   const int64_t rowZ = (int64_t)W * (2 * IntW<L>::W + 1) * m;  // words per row of A
   PolyView v;
   v.mon_off = a.mon_off;
@@ -758,9 +759,10 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
       }
       if constexpr (FZ) {
        if (act) {
-        // QD on the integer pipe throughout: the row, the start system's
-        // terms and the homotopy in limb-string arithmetic (a QD complex
-        // product on the FP64 pipe costs about 30 times a limb-string one)
+        // DD and QD on the integer pipe throughout: the row, the start
+        // system's terms and the homotopy in limb-string arithmetic (a QD
+        // complex product on the FP64 pipe costs about 30 times a limb-string
+        // one)
         using ZW = mpi::fz<IntW<L>::W>;
         constexpr int WZ = IntW<L>::W;
         mpi::fzs<IntW<L>::W> P[INT ? kIntMaxTrack : 1];
@@ -836,9 +838,11 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
       }
       __syncthreads();
       // ---- C: least squares J dx = -h by modified Gram-Schmidt
-      // QD solves on the integer pipe; a DD complex product is only 38 FP64
-      // instructions, and there the FP64 MGS was measured faster (1.6 s
-      // against 3.1 s for the whole n = 12, 4,096-path DD run)
+      // DD and QD with integer evaluation solve on the integer pipe, on the
+      // limb strings in A and R (for DD the FP64 MGS had been faster while
+      // every load and store converted: 1.6 s against 3.1 s for the n = 12,
+      // 4,096-path run; without conversions the integer path takes 1.08 s
+      // against 1.43 s)
       if constexpr (FZ)
         mgs_team_int<L, kIntMaxTrack>(FzStore<L>{reinterpret_cast<int32_t*>(a.A), m, p},
                                       FzStore<L>{reinterpret_cast<int32_t*>(a.R), m, p}, a.dx, n, n, m, p, act, warp,

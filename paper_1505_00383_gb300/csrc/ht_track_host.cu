@@ -306,10 +306,11 @@ int ht_track_paths_ex(ht_system* s, const int32_t* start_deg, const double* gamm
   const int nrhs = P.predictor > 0 ? 2 : 1;  // the tangent predictors add J v = -dh/dt
   // DD and QD (n <= 32) evaluate f and solve the Newton systems on the
   // integer pipe unless an FP64 variant was chosen for this system
-  // (ht_set_eval_config 0 or 1); QD then keeps A and R as limb strings of
-  // 2 W + 1 = 17 int32 words an entry (68 bytes against 64 for the doubles)
+  // (ht_set_eval_config 0 or 1), and keep A and R as limb strings of 2 W + 1
+  // int32 words an entry (QD 68 bytes against 64 for the doubles, DD 44
+  // against 32)
   const bool int_eval = L > 1 && s->d_coef_fz && n <= 32 && (s->eval_variant == -1 || s->eval_variant == 2);
-  const size_t ab = (int_eval && L == 4) ? (size_t)17 * 4 * m : cxb;  // bytes of one entry of A and R
+  const size_t ab = int_eval ? (size_t)(L == 4 ? 17 : 11) * 4 * m : cxb;  // bytes of one entry of A and R
   size_t o_xp = take(n * cxb), o_hx = take((size_t)cap * n * cxb), o_ht = take((size_t)cap * m * 8),
          o_A = take((size_t)n * (n + nrhs) * ab), o_R = take((size_t)n * (n + nrhs) * ab), o_dx = take(n * cxb),
          o_tx = P.predictor > 0 ? take((size_t)cap * n * cxb) : 0, o_tdx = P.predictor > 0 ? take(n * cxb) : 0,
