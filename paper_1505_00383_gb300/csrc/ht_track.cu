@@ -716,8 +716,31 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
         }
         for (int i = warp; i < n; i += T) {
           cx<L> acc = czero<L>();
-          for (int j = 0; j < mm; ++j)
-            acc = cadd(acc, cscale_r(ld<L>(a.hx, (int64_t)(base + j) * n + i, m, p), w[j]));
+          bool fz_done = false;
+          if constexpr (FZ && L == 4) {
+            // QD extrapolation on the integer pipe: the history points times
+            // their weights as limb-string products, summed exactly and
+            // rounded once (a QD complex-by-real product on the FP64 pipe is
+            // about 200 FP64 instructions)
+            if (!herm && !euler && mm > 0) {
+              constexpr int WZ = IntW<L>::W;
+              const double zero4[4] = {0.0, 0.0, 0.0, 0.0};
+              mpi::fz<WZ> terms[8];
+              int ones[8];
+              for (int j = 0; j < mm; ++j) {
+                const mpi::fz<WZ> wz = mpi::from_doubles<WZ, 4>(w[j].x, zero4);
+                terms[j] = mpi::mul<WZ>(fz_of<L>(ld<L>(a.hx, (int64_t)(base + j) * n + i, m, p)), wz);
+                ones[j] = 1;
+              }
+              double re[4], im[4];
+              mpi::to_doubles<WZ, 4>(mpi::sum<WZ, 8>(terms, ones, mm), re, im);
+              acc = cx_from<L>(re, im);
+              fz_done = true;
+            }
+          }
+          if (!fz_done)
+            for (int j = 0; j < mm; ++j)
+              acc = cadd(acc, cscale_r(ld<L>(a.hx, (int64_t)(base + j) * n + i, m, p), w[j]));
           if (herm) {
             acc = cscale_r(ld<L>(a.hx, (int64_t)(nh - 2) * n + i, m, p), ca);
             acc = cadd(acc, cscale_r(ld<L>(a.tx, (int64_t)(nh - 2) * n + i, m, p), cb));
