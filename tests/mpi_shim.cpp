@@ -362,3 +362,26 @@ extern "C" int mpi_scaled_convert(int L, int64_t n, const int32_t* a, int F, con
   else return -1;
   return 0;
 }
+
+// s * (ar + i ai) for fixed-point limb strings (n rows of WA int32 limbs per
+// component, frame F) and doubles s[n], as limb strings: out gets, per row,
+// the exponent and the W re and W im limbs (2 W + 1 int32).
+template <int WA, int W>
+static void scaled_fz(int64_t n, const int32_t* ar, const int32_t* ai, int F, const double* s, int32_t* out) {
+  for (int64_t q = 0; q < n; ++q) {
+    const fz<W> z = fixed_scaled_to_fz<WA, W>(ar + q * WA, ai + q * WA, F, s[q]);
+    int32_t* o = out + q * (2 * W + 1);
+    o[0] = z.f;
+    for (int k = 0; k < W; ++k) {
+      o[1 + k] = z.r[k];
+      o[1 + W + k] = z.i[k];
+    }
+  }
+}
+extern "C" int mpi_scaled_fz(int L, int64_t n, const int32_t* ar, const int32_t* ai, int F, const double* s,
+                             int32_t* out) {
+  if (L == 2) scaled_fz<4, 5>(n, ar, ai, F, s, out);
+  else if (L == 4) scaled_fz<8, 8>(n, ar, ai, F, s, out);
+  else return -1;
+  return 0;
+}

@@ -287,3 +287,40 @@ def test_scaled_conversion_is_the_truncated_exact_product(shim, L):
         assert abs(exact - got) <= abs(exact) * Fraction(2) ** (1 - 53 * L), (q, float(exact), float(got))
         if s[q] == 1.0:
             assert np.array_equal(out[q], plain[q])
+
+
+@pytest.mark.parametrize("L", [2, 4])
+def test_scaled_limb_string_is_the_exact_product_cut_to_w_limbs(shim, L):
+    """s (ar + i ai) for fixed-point strings and a double s, as a limb string
+    (the tracker's Jacobian rows scaled by t): each component of the string's
+    value lies within one unit of its last limb of the exact product (the
+    string keeps the W limbs from the highest nonzero one of either
+    component), its lower limbs are digits in [0, 2^29), and the top limbs
+    stay below 2^28 in magnitude.  Exact rationals on the Python side."""
+    from fractions import Fraction
+    WA, W = {2: (4, 5), 4: (8, 8)}[L]
+    F = -29 * (WA - 1) - 3
+    rng = np.random.default_rng(700 + L)
+    n = 300
+    ar = rng.integers(0, 1 << 29, size=(n, WA)).astype(np.int32)
+    ai = rng.integers(0, 1 << 29, size=(n, WA)).astype(np.int32)
+    ar[:, -1] = rng.integers(-(1 << 27), 1 << 27, size=n)
+    ai[:, -1] = rng.integers(-(1 << 27), 1 << 27, size=n)
+    ai[::5] = 0  # real values
+    ar[::11, :-2] = 0  # short strings
+    s = rng.uniform(0.0, 1.0, n)
+    s[:4] = [1.0, 0.5, 2.0 ** -40, 1.0 - 2.0 ** -53]
+    out = np.zeros((n, 2 * W + 1), dtype=np.int32)
+    shim.mpi_scaled_fz.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                                   ctypes.c_void_p, ctypes.c_void_p]
+    assert shim.mpi_scaled_fz(L, n, _p(ar), _p(ai), F, _p(s), _p(out)) == 0
+    two = Fraction(2)
+    for q in range(n):
+        f = int(out[q, 0])
+        for comp, a in ((0, ar[q]), (1, ai[q])):
+            limbs = out[q, 1 + comp * W:1 + (comp + 1) * W]
+            assert np.all(limbs[:-1] >= 0) and np.all(limbs[:-1] < (1 << 29))
+            assert abs(int(limbs[-1])) < (1 << 28)
+            exact = sum(Fraction(int(a[k])) * two ** (29 * k) for k in range(WA)) * two ** F * Fraction(float(s[q]))
+            got = sum(Fraction(int(limbs[k])) * two ** (29 * k) for k in range(W)) * two ** f
+            assert abs(exact - got) <= two ** (f + 1), (q, comp)
