@@ -559,7 +559,7 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
   __shared__ double sh_h[32];       // learned step of each lane's path
   __shared__ double sh_alpha[32];   // learned tangent correction of each lane's path
   __shared__ long long sh_slot[32]; // trace record slot of each lane's path (-1: none)
-  __shared__ double sh_w[8][L][32]; // extrapolation weights of each lane's step, [point][limb][lane]
+  __shared__ double sh_w[L > 1 ? 8 : 1][L][32];  // extrapolation weights (DD, QD), [point][limb][lane]
   // The network's weights are read from the device image (L1/L2): staging
   // them in shared memory would enlarge the shared-memory carveout and take
   // L1 capacity from the Newton workspace.  Only warp 0's sample staging
@@ -673,24 +673,32 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
       const bool euler = start && !herm && pmode >= 1 && ntan >= 1;
       const int mm = !start ? 0 : ((herm || euler) ? 0 : (pmode >= 1 ? 1 : min(nh, a.prm.max_order + 1)));
       const int base = nh - mm;
+      // weight of history point j (Lagrange, at t1)
+      auto weight = [&](int j) {
+        rl<L> num = r_from<L>(1.0), den = r_from<L>(1.0);
+        double tj = a.ht[(int64_t)(base + j) * m + p];
+        for (int i = 0; i < mm; ++i) {
+          if (i == j) continue;
+          double ti = a.ht[(int64_t)(base + i) * m + p];
+          num = r_mul(num, r_diff<L>(t1, ti));
+          den = r_mul(den, r_diff<L>(tj, ti));
+        }
+        return r_div(num, den);
+      };
       if (start) {
         double step = fmin(h, 1.0 - t);
         t1 = (step >= 1.0 - t) ? 1.0 : t + step;
-        for (int j = warp; j < mm; j += T) {
-          rl<L> num = r_from<L>(1.0), den = r_from<L>(1.0);
-          double tj = a.ht[(int64_t)(base + j) * m + p];
-          for (int i = 0; i < mm; ++i) {
-            if (i == j) continue;
-            double ti = a.ht[(int64_t)(base + i) * m + p];
-            num = r_mul(num, r_diff<L>(t1, ti));
-            den = r_mul(den, r_diff<L>(tj, ti));
-          }
-          const rl<L> wj = r_div(num, den);
+        if constexpr (L > 1) {
+          for (int j = warp; j < mm; j += T) {
+            const rl<L> wj = weight(j);
 #pragma unroll
-          for (int l = 0; l < L; ++l) sh_w[j][l][lane] = r_limb(wj, l);
+            for (int l = 0; l < L; ++l) sh_w[j][l][lane] = r_limb(wj, l);
+          }
         }
       }
-      __syncthreads();
+      // (in double a weight is a few instructions: every warp computes them,
+      // without the barrier)
+      if constexpr (L > 1) __syncthreads();
       if (start) {
         // tangent predictors: cubic Hermite on the last two points and their
         // tangents, Euler on the last one; until a tangent exists, x itself
@@ -709,10 +717,14 @@ __global__ void __launch_bounds__(32 * MAXT, MAXT > 8 ? 1 : (L == 1 ? 3 : (L == 
         }
         rl<L> w[8];
         for (int j = 0; j < mm; ++j) {
-          double wl[L];
+          if constexpr (L > 1) {
+            double wl[L];
 #pragma unroll
-          for (int l = 0; l < L; ++l) wl[l] = sh_w[j][l][lane];
-          w[j] = r_of<L>(wl);
+            for (int l = 0; l < L; ++l) wl[l] = sh_w[j][l][lane];
+            w[j] = r_of<L>(wl);
+          } else {
+            w[j] = weight(j);
+          }
         }
         for (int i = warp; i < n; i += T) {
           cx<L> acc = czero<L>();
