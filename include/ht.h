@@ -173,11 +173,11 @@ int ht_eval_diff_unfused(ht_system* sys, int64_t n_pts, const double* x, double*
  * (a small multiple of 2^(-53 L) times the sum of the moduli of the terms of
  * each output) with its own rounding.
  * The choice also applies inside ht_track_paths for DD and QD systems with
- * n <= 32: by default (and with variant 2) the tracker evaluates f on the
- * integer pipe, and for QD also solves the Newton systems there
- * (ht_mgs_solve_ex variant 2); with variant 0 or 1 it uses the FP64 pipe
- * throughout (variant 3 counts as FP64 there).  Double systems always track
- * on the FP64 pipe.
+ * n <= 32: by default (and with variant 2) the tracker runs its Newton round
+ * on the integer pipe: f and its Jacobian rows, the homotopy terms and the
+ * least squares (the arithmetic of ht_mgs_solve_ex variant 2) in limb
+ * strings; with variant 0 or 1 it uses the FP64 pipe throughout (variant 3
+ * counts as FP64 there).  Double systems always track on the FP64 pipe.
  */
 int ht_set_eval_config(ht_system* sys, int variant, int threads);
 
